@@ -1,0 +1,300 @@
+"""Benchmark of the FOT hot path on GB300: FOT Mpixel*iter/s at 1024^2.
+
+One step = one whole solve of the benchmark workload through the C ABI: problem load
+(a = g^2/sum g^2, logs), 200 Sinkhorn iterations (Eqs. 7-8, 4 axis passes each) and the
+phase step (moments of Eqs. 9-10 + trapezoid integration).  Workload: 1024 x 1024
+two-Gaussian input beam -> seeded composite of 12 flat-top rectangles / disks / rings at
+30% coverage, fixed eps = 2e-4 n^2 px^2 (the paper's working eps), 200 iterations.
+Inputs are synthetic (seeded); they stand in for the paper's Fig. 1 images.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank solves its own copy of the
+workload (independent problems, no collective on the data path): weak scaling.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FOT Mpixel*iter/s at 1024^2 (mixed vs FP32, <=1e-4 marginal L1); % of roofline"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fot", choices=["fot", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    p.add_argument("--n", type=int, default=1024)
+    p.add_argument("--iters", type=int, default=200)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(n, iters):
+    from paper_2512_19072_gb300 import inputs
+    w = inputs.config3(n, iters=iters)
+    return w
+
+
+# ----------------------------------------------------------------------------------------
+# CPU side: the FP64 oracle, as it stands, on a bounded sample
+# ----------------------------------------------------------------------------------------
+def _oracle_sample(w, rows, budget_s):
+    """Time the oracle's axis pass (its exact FP64 log-sum-exp) on `rows` input rows of the
+    workload, repeated until `budget_s` elapsed.  One FOT iteration is 4 passes over n rows,
+    so the time of one iteration is (time per row) * 4 n."""
+    import torch
+    from oracle import fot
+    n = w.g.shape[0]
+    eps = float(w.eps[0])
+    psi = np.full((rows, n), eps * math.log(1.0 / (n * n)))
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        fot.axis_lse(psi / eps, eps)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    per_row = el / (reps * rows)
+    t_iter = per_row * 4 * n
+    return {"value": n * n / t_iter / 1e6, "unit": "Mpixel*iter/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{reps} x FP64 oracle axis pass over {rows} of {n} rows at n={n} "
+                      f"(eps={eps:.4g} px^2); one iteration = 4 n row-passes, scaled"}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    w = _workload(a.n, a.iters)
+    vals = []
+    for i in range(a.warmup + a.steps):
+        s = _oracle_sample(w, rows=16, budget_s=2.0)
+        if i >= a.warmup:
+            vals.append(s["value"])
+    v = statistics.median(vals)
+    s["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mpixel*iter/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": a.n * a.n / (v * 1e6) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": a.n, "iters_per_solve": a.iters,
+                       "eps_px2": float(w.eps[0]), "step": "one FP64 oracle iteration (sampled)"},
+            "cpu_baseline": s,
+            "e2e": {"value": v, "unit": "Mpixel*iter/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# GPU side
+# ----------------------------------------------------------------------------------------
+class _Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.rows = []
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# MUFU ex2 issue rate used as the ALU roofline of the exact FP32 pass: 32 ex2 per clock
+# per SM on sm_103 (GB300 doubles the sm_100 special-function rate for exponentials),
+# times 152 SMs and the maximum SM clock.
+EX2_PER_CLK_PER_SM = 32
+N_SM = 152
+
+
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    from paper_2512_19072_gb300 import binding as B
+
+    w = _workload(a.n, a.iters)
+    n = a.n
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    eps = w.eps
+    prec = B.FOT_MIXED if a.precision == "mixed" else B.FOT_FP32
+    ctx = B.fot_create(n, n, prec)
+    phi = ctx.empty()
+    Dx = ctx.empty()
+    Dy = ctx.empty()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.fot_solve(ctx, g, G, eps, a.iters)
+        B._check(B._lib.fot_phase(ctx._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = _Clocks(dev)
+    l0 = B.fot_launch_count(ctx)
+    evs = []
+    loop_ms = []
+    passes = 0
+    for _ in range(a.steps):
+        flush.zero_()                       # L2 flush between steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+        ms_loop, passes = B.fot_loop_time(ctx)
+        loop_ms.append(ms_loop)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = B.fot_launch_count(ctx) - l0
+    clk = clocks.stop()
+    step_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
+    if ws > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = ws * n * n * a.iters / (step_ms * 1e-3) / 1e6
+
+    line = None
+    if rank == 0:
+        l1, dual = B.fot_marginal_error(ctx)
+        # roofline of the dominant kernel (the axis pass; only axis passes run in the loop)
+        pass_ms = statistics.median(loop_ms) / max(passes, 1)
+        peaks, peak_src = _peaks()
+        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        ex2_per_pass = float(n) * n * n                   # one exponential per (row, out, term)
+        achieved = ex2_per_pass / (pass_ms * 1e-3) / 1e12  # Tex2/s
+        peak = EX2_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "axis_pass_kernel (exact FP32 log-sum-exp axis pass)",
+                "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz "
+                               f"(max SM clock, {peak_src} peaks file)",
+                "pass_ms": pass_ms}
+        # end to end through the C ABI with host buffers (H2D of g, G and D2H of phi per step)
+        gh = torch.from_numpy(w.g.astype(np.float32)).pin_memory()
+        Gh = torch.from_numpy(w.G.astype(np.float32)).pin_memory()
+        ph = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        B.fot_solve_phase_host(ctx, gh, Gh, eps, a.iters, phi_host=ph)
+        t_e2e = []
+        for _ in range(max(2, a.steps // 2)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.fot_solve_phase_host(ctx, gh, Gh, eps, a.iters, phi_host=ph)
+            t_e2e.append(time.perf_counter() - t0)
+        e2e_v = n * n * a.iters / statistics.median(t_e2e) / 1e6
+        cpu = None
+        if not a.no_cpu_baseline and ws == 1:
+            cpu = _oracle_sample(w, rows=32, budget_s=12.0)
+        line = {"metric": METRIC, "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if a.precision == "fp32" else "bf16+f32",
+                "data": "synthetic (seeded two-Gaussian beam -> 12-shape composite target)",
+                "config": {"workload": w.name, "n": n, "iters_per_solve": a.iters,
+                           "eps_px2": float(eps[0]), "eps_paper": 2e-4,
+                           "precision": a.precision,
+                           "step": "fot_solve (prep + 200 iterations) + fot_phase",
+                           "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"replicas x{ws} (independent problems)"},
+                "marginal_l1": l1, "dual_objective": dual,
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_v, "unit": "Mpixel*iter/s",
+                        "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4},
+                "gpu_launches": launches, "clocks": clk,
+                "paper_context": "1024^2, 200 iterations: 76 s Core i7 (2.76 Mpixel*iter/s), "
+                                 "8.5 s T4 (24.7 Mpixel*iter/s)"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_gpu(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * fot.h -- C ABI of the FOT (Fast Optimal Transport) dual-potential iteration on GB300
+ * (sm_103a), after Torchylo, Swan, Tellez and Hogan, "A fast, large-scale optimal
+ * transport algorithm for holographic beam shaping".
+ *
+ * The method (Sec. 2-3, Algorithm 1): given an input-beam amplitude g_jk and a target
+ * amplitude G_LM on n_r x n_c pixel grids, run entropic Sinkhorn iterations
+ *     u <- g^2 / (Lambda V Lambda)      (Eq. 7)
+ *     V <- G^2 / (Lambda u Lambda)      (Eq. 8)
+ * with the separable Gaussian kernel Lambda_jK = exp(-(j-K)^2 / (2 eps)), then recover the
+ * phase from the first moments of the plan Gamma = u exp(-C/eps) V (Eqs. 9-10) and
+ * integrate it with the trapezoid rule.  The library works in the log domain,
+ * f = eps log u and psi = eps log V ("potentials", px^2 units), which is the same
+ * iteration without exponent overflow.
+ *
+ * Conventions shared by every entry point
+ *  - Images are row-major float32, rows x cols, element (j, k) at j*cols + k; row index j
+ *    is the x axis, column index k the y axis (Sec. 2).  g and G share one shape.
+ *  - Unless stated otherwise, pointers are DEVICE pointers on the context's device,
+ *    owned by the caller; the context never keeps a caller pointer after a call returns.
+ *  - eps is in px^2 (cost ((j-L)^2 + (k-M)^2)/2).  FOT_EPS_PAPER selects the paper's units,
+ *    whose cost carries an extra 1/n^2 (Eq. 3): eps_px = n^2 * eps_paper, n = max(rows, cols).
+ *  - All device work is enqueued on the context's stream and is asynchronous.  Argument
+ *    errors are returned at once.  Errors found on the device (negative or non-finite
+ *    amplitudes: FOT_EINVAL; zero total power: FOT_EMASS; a non-finite potential during
+ *    the iteration: FOT_ENONFINITE) are latched in the context and returned by the next
+ *    synchronising call (fot_sync, fot_potentials, fot_phase, fot_marginal_error), after
+ *    which further enqueued work of that context is skipped until the next fot_solve or
+ *    fot_set_problem clears the latch.
+ *  - Zero-mass pixels (g = 0 or G = 0) carry potential -INFINITY.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef FOT_H_
+#define FOT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fot_ctx fot_ctx;
+
+typedef enum {
+  FOT_OK = 0,
+  FOT_EINVAL = 1,        /* bad argument, or negative / non-finite amplitude */
+  FOT_ENOMEM = 2,        /* device or host allocation failed */
+  FOT_ECUDA = 3,         /* a CUDA runtime call failed */
+  FOT_ENONFINITE = 4,    /* a potential became NaN / +inf during the iteration */
+  FOT_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  FOT_EMASS = 6,         /* g or G has zero total power */
+  FOT_EUNSUPPORTED = 7,  /* precision or shape not supported by this build */
+  FOT_ESTATE = 8         /* call out of order (e.g. fot_phase before fot_solve) */
+} fot_status;
+
+typedef enum {
+  FOT_FP32 = 0,          /* exact log-sum-exp axis passes, FP32 on the CUDA cores */
+  FOT_MIXED = 1          /* axis GEMMs on tcgen05 tensor cores (BF16 operands, FP32
+                            accumulation) with FP32 log-domain potentials; falls back
+                            per output to the exact FP32 pass where the offsets leave
+                            the BF16 exponent range */
+} fot_precision;
+
+typedef enum { FOT_EPS_PX2 = 0, FOT_EPS_PAPER = 1 } fot_eps_units;
+
+/* Create a context for rows x cols problems on `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Allocates all device scratch:
+ * about 10 rows*cols float32 buffers plus small reduction scratch.
+ * Returns FOT_EINVAL for rows or cols outside [1, 4096], FOT_ENOMEM on allocation failure. */
+fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int device,
+                      void* cuda_stream);
+
+/* Release every device buffer of the context (synchronises its stream first). */
+void fot_destroy(fot_ctx* ctx);
+
+/* Replace the stream later calls enqueue on. */
+fot_status fot_set_stream(fot_ctx* ctx, void* cuda_stream);
+
+/* Load a problem (Sec. 2: marginal constraints g^2 and G^2): a = g^2 / sum g^2 and
+ * b = G^2 / sum G^2 (both renormalised to unit mass) and their logs.  g, G: device,
+ * rows x cols.  Clears the device error latch. */
+fot_status fot_set_problem(fot_ctx* ctx, const float* g, const float* G);
+
+/* Algorithm 1: load the problem (as fot_set_problem), set V = 1/(rows*cols), and run
+ * `iters` iterations of Eqs. 7-8.  eps: host array of n_eps values; n_eps == 1 is a fixed
+ * eps, n_eps == iters gives iteration t the value eps[t] (an annealing schedule; the
+ * potentials keep px^2 units across changes).  dx: input-plane grid spacing used by
+ * fot_phase (Sec. 2: x_j = (j - floor(n/2)) dx; dx <= 0 selects 1/sqrt(n), the paper's
+ * units).  Stops after a fixed number of iterations (the paper's practice). */
+fot_status fot_solve(fot_ctx* ctx, const float* g, const float* G, double dx,
+                     const double* eps, int n_eps, int eps_units, int iters);
+
+/* Continue the current problem for `iters` more iterations from the potentials the
+ * context holds (checkpoint / resume).  Same eps rules as fot_solve. */
+fot_status fot_resume(fot_ctx* ctx, const double* eps, int n_eps, int eps_units, int iters);
+
+/* Wait for the context's stream; return the latched device status. */
+fot_status fot_sync(fot_ctx* ctx);
+
+/* Copy out f = eps log u and psi = eps log V (px^2; -INFINITY on zero mass).  Either
+ * pointer may be NULL.  Synchronising. */
+fot_status fot_potentials(fot_ctx* ctx, float* f_out, float* psi_out);
+
+/* Load caller potentials (device, px^2) as the solver state, e.g. to resume from a
+ * checkpoint taken with fot_potentials.  f may be NULL (only psi is read by the next
+ * iteration). */
+fot_status fot_set_potentials(fot_ctx* ctx, const float* f, const float* psi);
+
+/* Phase retrieval (Eqs. 9-10 and the trapezoid "Integrate" step of Algorithm 1):
+ *   dphidx_jk = (u/g^2)_jk sum_LM Lambda_jL X_L V_LM Lambda_kM,  dphidy likewise with Y_M,
+ * with u from the last u-update and V the final V, X_L = (L - floor(rows/2)) / (rows dx),
+ * Y_M = (M - floor(cols/2)) / (cols dx); phi (cycles) integrates them with the trapezoid
+ * rule from phi = 0 at the grid centre, first down the centre column (k = floor(cols/2))
+ * with dphidx, then along every row with dphidy.  Any output may be NULL.  Synchronising. */
+fot_status fot_phase(fot_ctx* ctx, float* phi_out, float* dphidx_out, float* dphidy_out);
+
+/* Marginal violation of the current iterate, ||Gamma 1 - a||_1 + ||Gamma^T 1 - b||_1
+ * (the total-variation convergence measure of Sec. 3, times two), from one extra exact
+ * FP32 u-half-step evaluated on the stored potentials (never with the mixed-precision
+ * kernels); accumulated in double.  Also returns the entropic dual objective
+ * <f,a> + <psi,b> - eps sum Gamma + eps when dual_out != NULL.  Synchronising. */
+fot_status fot_marginal_error(fot_ctx* ctx, double* l1_out, double* dual_out);
+
+/* One half-step from caller potentials, for verification and custom loops:
+ *   fot_u_update: f = eps (log a - S), S = log(Lambda exp(psi/eps) Lambda)   (Eq. 7)
+ *   fot_v_update: psi = eps (log b - T), T = log(Lambda exp(f/eps) Lambda)   (Eq. 8)
+ * using the problem last loaded.  pot_in, pot_out: device rows x cols px^2; logsum_out
+ * (S or T, natural log) may be NULL.  eps in px^2. */
+fot_status fot_u_update(fot_ctx* ctx, const float* psi_in, double eps, float* f_out,
+                        float* logsum_out);
+fot_status fot_v_update(fot_ctx* ctx, const float* f_in, double eps, float* psi_out,
+                        float* logsum_out);
+
+/* Exact c-transform, the eps -> 0 limit of a half-step (the log a term vanishes):
+ *   out_jk = min_LM [ ((j-L)^2 + (k-M)^2)/2 - pot_LM ],
+ * by a lower envelope of parabolas along each row, then along each column.  -INFINITY
+ * entries of pot are excluded; rows x cols device buffers, px^2. */
+fot_status fot_c_transform(fot_ctx* ctx, const float* pot_in, float* out);
+
+/* End-to-end convenience: HOST float32 g, G in; HOST float32 phi out (rows x cols).
+ * Copies in, runs fot_solve and fot_phase, copies out; synchronising. */
+fot_status fot_solve_phase_host(fot_ctx* ctx, const float* g_host, const float* G_host,
+                                double dx, const double* eps, int n_eps, int eps_units,
+                                int iters, float* phi_host);
+
+/* Number of kernels this context has launched since creation (for launch accounting). */
+int64_t fot_launch_count(const fot_ctx* ctx);
+
+/* Device time (CUDA events on the context stream) of the Sinkhorn loop of the last
+ * fot_solve / fot_resume, and the number of axis-pass kernels it launched (4 per iteration
+ * on the FP32 path).  Only axis passes run inside that loop, so ms / passes is their mean
+ * duration.  Synchronises with the end of the loop. */
+fot_status fot_loop_time(fot_ctx* ctx, double* ms_out, int64_t* passes_out);
+
+const char* fot_status_string(fot_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOT_H_ */

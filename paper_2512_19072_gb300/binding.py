@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libfot.so (include/fot.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes torch CUDA
+tensors (float32, contiguous, rows x cols) where the C call takes device pointers; the
+stream is the current torch stream.  All arithmetic of the method runs in the library's
+CUDA kernels.  Importing this module raises if libfot.so has not been built: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfot.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2512_19072_gb300.build` "
+                      "(the FOT path has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FOT_FP32, FOT_MIXED = 0, 1
+FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
+STATUS = {0: "FOT_OK", 1: "FOT_EINVAL", 2: "FOT_ENOMEM", 3: "FOT_ECUDA", 4: "FOT_ENONFINITE",
+          5: "FOT_ETIMEOUT", 6: "FOT_EMASS", 7: "FOT_EUNSUPPORTED", 8: "FOT_ESTATE"}
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "fot_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _P]),
+    "fot_destroy": (None, [_P]),
+    "fot_set_stream": (_I, [_P, _P]),
+    "fot_set_problem": (_I, [_P, _P, _P]),
+    "fot_solve": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I]),
+    "fot_resume": (_I, [_P, _DP, _I, _I, _I]),
+    "fot_sync": (_I, [_P]),
+    "fot_potentials": (_I, [_P, _P, _P]),
+    "fot_set_potentials": (_I, [_P, _P, _P]),
+    "fot_phase": (_I, [_P, _P, _P, _P]),
+    "fot_marginal_error": (_I, [_P, _DP, _DP]),
+    "fot_u_update": (_I, [_P, _P, _D, _P, _P]),
+    "fot_v_update": (_I, [_P, _P, _D, _P, _P]),
+    "fot_c_transform": (_I, [_P, _P, _P]),
+    "fot_solve_phase_host": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _P]),
+    "fot_launch_count": (ctypes.c_int64, [_P]),
+    "fot_loop_time": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    "fot_status_string": (ctypes.c_char_p, [_I]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class FotError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.fot_status_string(status).decode()
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+
+
+def _check(status, where):
+    if status != 0:
+        raise FotError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _eps_arr(eps):
+    e = np.ascontiguousarray(np.atleast_1d(np.asarray(eps, dtype=np.float64)))
+    return e, e.ctypes.data_as(_DP), len(e)
+
+
+class Context:
+    """Owns one fot_ctx (rows x cols) and the device scratch it allocates."""
+
+    def __init__(self, rows, cols, precision=FOT_FP32, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.rows, self.cols, self.device = rows, cols, device
+        h = _P()
+        with torch.cuda.device(device):
+            _check(_lib.fot_create(ctypes.byref(h), rows, cols, precision, device, _stream()),
+                   "fot_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fot_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def _sync_stream(self):
+        _lib.fot_set_stream(self._h, _stream())
+
+    def empty(self):
+        return torch.empty((self.rows, self.cols), dtype=torch.float32, device=f"cuda:{self.device}")
+
+
+def fot_create(rows, cols, precision=FOT_FP32, device=None):
+    return Context(rows, cols, precision, device)
+
+
+def fot_destroy(ctx):
+    ctx.close()
+
+
+def fot_set_problem(ctx, g, G):
+    ctx._sync_stream()
+    _check(_lib.fot_set_problem(ctx._h, _ptr(g), _ptr(G)), "fot_set_problem")
+
+
+def fot_solve(ctx, g, G, eps, iters=None, dx=0.0, eps_units=FOT_EPS_PX2):
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    ctx._sync_stream()
+    _check(_lib.fot_solve(ctx._h, _ptr(g), _ptr(G), float(dx), ep, ne, eps_units, int(iters)),
+           "fot_solve")
+
+
+def fot_resume(ctx, eps, iters=None, eps_units=FOT_EPS_PX2):
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    ctx._sync_stream()
+    _check(_lib.fot_resume(ctx._h, ep, ne, eps_units, int(iters)), "fot_resume")
+
+
+def fot_sync(ctx):
+    _check(_lib.fot_sync(ctx._h), "fot_sync")
+
+
+def fot_potentials(ctx):
+    f, psi = ctx.empty(), ctx.empty()
+    ctx._sync_stream()
+    _check(_lib.fot_potentials(ctx._h, _ptr(f), _ptr(psi)), "fot_potentials")
+    return f, psi
+
+
+def fot_set_potentials(ctx, f, psi):
+    ctx._sync_stream()
+    _check(_lib.fot_set_potentials(ctx._h, _ptr(f), _ptr(psi)), "fot_set_potentials")
+
+
+def fot_phase(ctx):
+    phi, dx, dy = ctx.empty(), ctx.empty(), ctx.empty()
+    ctx._sync_stream()
+    _check(_lib.fot_phase(ctx._h, _ptr(phi), _ptr(dx), _ptr(dy)), "fot_phase")
+    return phi, dx, dy
+
+
+def fot_marginal_error(ctx):
+    l1, dual = ctypes.c_double(), ctypes.c_double()
+    ctx._sync_stream()
+    _check(_lib.fot_marginal_error(ctx._h, ctypes.byref(l1), ctypes.byref(dual)),
+           "fot_marginal_error")
+    return l1.value, dual.value
+
+
+def fot_u_update(ctx, psi, eps, with_logsum=False):
+    f = ctx.empty()
+    S = ctx.empty() if with_logsum else None
+    ctx._sync_stream()
+    _check(_lib.fot_u_update(ctx._h, _ptr(psi), float(eps), _ptr(f), _ptr(S)), "fot_u_update")
+    return (f, S) if with_logsum else f
+
+
+def fot_v_update(ctx, f, eps, with_logsum=False):
+    psi = ctx.empty()
+    T = ctx.empty() if with_logsum else None
+    ctx._sync_stream()
+    _check(_lib.fot_v_update(ctx._h, _ptr(f), float(eps), _ptr(psi), _ptr(T)), "fot_v_update")
+    return (psi, T) if with_logsum else psi
+
+
+def fot_c_transform(ctx, pot):
+    out = ctx.empty()
+    ctx._sync_stream()
+    _check(_lib.fot_c_transform(ctx._h, _ptr(pot), _ptr(out)), "fot_c_transform")
+    return out
+
+
+def fot_solve_phase_host(ctx, g_host, G_host, eps, iters=None, dx=0.0, eps_units=FOT_EPS_PX2,
+                         phi_host=None):
+    """g_host, G_host: pinned (or pageable) CPU float32 tensors; returns phi on the host."""
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    if phi_host is None:
+        phi_host = torch.empty((ctx.rows, ctx.cols), dtype=torch.float32, pin_memory=True)
+    for t in (g_host, G_host, phi_host):
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("expected contiguous float32 host tensors")
+    ctx._sync_stream()
+    _check(_lib.fot_solve_phase_host(ctx._h, ctypes.c_void_p(g_host.data_ptr()),
+                                     ctypes.c_void_p(G_host.data_ptr()), float(dx), ep, ne,
+                                     eps_units, int(iters), ctypes.c_void_p(phi_host.data_ptr())),
+           "fot_solve_phase_host")
+    return phi_host
+
+
+def fot_launch_count(ctx):
+    return int(_lib.fot_launch_count(ctx._h))
+
+
+def fot_loop_time(ctx):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(_lib.fot_loop_time(ctx._h, ctypes.byref(ms), ctypes.byref(n)), "fot_loop_time")
+    return ms.value, n.value
+
+
+def exported_symbols():
+    return list(_SIGS)

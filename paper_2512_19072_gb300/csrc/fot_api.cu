@@ -1,0 +1,335 @@
+// C ABI of the FOT library (include/fot.h): context lifetime, argument checking, the
+// Sinkhorn loop of Algorithm 1 and the phase step, on top of the kernels in fot_simt.cu
+// (exact FP32 passes), fot_tc.cu (tensor-core passes) and fot_ctransform.cu.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fot_common.cuh"
+
+namespace fot {
+void half_step_simt(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
+                    float* pot_out, float* logsum, float* tmp);
+void moments_simt(fot_ctx* c, double eps, double dx, float* Dx, float* Dy);
+void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
+void fill(fot_ctx* c, float* p, size_t N, float v);
+void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
+                    const float* T, double eps, double* out);
+void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, float* phi);
+void c_transform_envelope(fot_ctx* c, const float* pot_in, float* out);
+// tensor-core path (fot_tc.cu)
+bool tc_supported(int rows, int cols);
+int tc_create(fot_ctx* c);
+void tc_destroy(fot_ctx* c);
+void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
+                  float* pot_out, float* logsum);
+}  // namespace fot
+
+using namespace fot;
+
+static const int kMaxDim = 4096;
+
+#define FOT_CUDA(call)                                \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return FOT_ECUDA;          \
+  } while (0)
+
+static fot_status check_launch(fot_ctx* c) {
+  (void)c;
+  return cudaGetLastError() == cudaSuccess ? FOT_OK : FOT_ECUDA;
+}
+
+static fot_status read_latched(fot_ctx* c) {
+  int e = 0;
+  FOT_CUDA(cudaMemcpyAsync(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  FOT_CUDA(cudaStreamSynchronize(c->stream));
+  return (fot_status)e;
+}
+
+static bool bad_ptr(const void* p) { return p == nullptr; }
+
+static double eps_px(const fot_ctx* c, double e, int units) {
+  if (units == FOT_EPS_PAPER) {
+    const double n = (double)(c->rows > c->cols ? c->rows : c->cols);
+    return e * n * n;
+  }
+  return e;
+}
+
+static fot_status check_eps(const double* eps, int n_eps, int iters) {
+  if (iters < 0 || eps == nullptr || n_eps < 1) return FOT_EINVAL;
+  if (!(n_eps == 1 || n_eps == iters)) return FOT_EINVAL;
+  for (int i = 0; i < n_eps; ++i)
+    if (!(eps[i] > 0.0) || !isfinite(eps[i])) return FOT_EINVAL;
+  return FOT_OK;
+}
+
+extern "C" {
+
+const char* fot_status_string(fot_status s) {
+  switch (s) {
+    case FOT_OK: return "ok";
+    case FOT_EINVAL: return "invalid argument or input (negative / non-finite amplitude)";
+    case FOT_ENOMEM: return "out of memory";
+    case FOT_ECUDA: return "CUDA runtime error";
+    case FOT_ENONFINITE: return "non-finite potential during the iteration";
+    case FOT_ETIMEOUT: return "bounded device wait timed out";
+    case FOT_EMASS: return "zero total power in g or G";
+    case FOT_EUNSUPPORTED: return "unsupported precision or shape";
+    case FOT_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int device,
+                      void* cuda_stream) {
+  if (!out) return FOT_EINVAL;
+  *out = nullptr;
+  if (rows < 1 || cols < 1 || rows > kMaxDim || cols > kMaxDim) return FOT_EINVAL;
+  if (precision != FOT_FP32 && precision != FOT_MIXED) return FOT_EINVAL;
+  if (getenv("FOT_FAULT_INJECT_ENOMEM")) return FOT_ENOMEM;   // host-side fault injection
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(device));
+  fot_ctx* c = new (std::nothrow) fot_ctx();
+  if (!c) return FOT_ENOMEM;
+  c->rows = rows;
+  c->cols = cols;
+  c->device = device;
+  c->precision = precision;
+  c->stream = (cudaStream_t)cuda_stream;
+  const size_t N = (size_t)rows * cols;
+  c->red_blocks = (int)((N + 1023) / 1024 < 1024 ? (N + 1023) / 1024 : 1024);
+  if (c->red_blocks < 1) c->red_blocks = 1;
+  float** bufs[] = {&c->la, &c->lb, &c->f, &c->psi, &c->R, &c->R2, &c->S_last, &c->tmp, &c->tmp2,
+                    &c->phi};
+  bool ok = true;
+  for (float** b : bufs) ok = ok && cudaMalloc((void**)b, N * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->col_phi, (size_t)rows * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->red, (size_t)(4 * c->red_blocks + 16) * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) == cudaSuccess;
+  if (ok) ok = cudaEventCreate(&c->ev_loop0) == cudaSuccess && cudaEventCreate(&c->ev_loop1) == cudaSuccess;
+  if (ok && precision == FOT_MIXED) {
+    if (!tc_supported(rows, cols)) {
+      fot_destroy(c);
+      return FOT_EUNSUPPORTED;
+    }
+    ok = tc_create(c) == 0;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    fot_destroy(c);
+    return FOT_ENOMEM;
+  }
+  *out = c;
+  return FOT_OK;
+}
+
+void fot_destroy(fot_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->tc) tc_destroy(c);
+  float* bufs[] = {c->la, c->lb, c->f, c->psi, c->R, c->R2, c->S_last, c->tmp, c->tmp2, c->phi,
+                   c->col_phi};
+  for (float* b : bufs)
+    if (b) cudaFree(b);
+  if (c->red) cudaFree(c->red);
+  if (c->err) cudaFree(c->err);
+  if (c->ev_loop0) cudaEventDestroy(c->ev_loop0);
+  if (c->ev_loop1) cudaEventDestroy(c->ev_loop1);
+  delete c;
+}
+
+fot_status fot_set_stream(fot_ctx* c, void* s) {
+  if (!c) return FOT_EINVAL;
+  c->stream = (cudaStream_t)s;
+  return FOT_OK;
+}
+
+int64_t fot_launch_count(const fot_ctx* c) { return c ? c->launches : -1; }
+
+fot_status fot_loop_time(fot_ctx* c, double* ms_out, int64_t* passes_out) {
+  if (!c || !ms_out) return FOT_EINVAL;
+  if (!c->have_solution) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  FOT_CUDA(cudaEventSynchronize(c->ev_loop1));
+  float ms = 0.f;
+  FOT_CUDA(cudaEventElapsedTime(&ms, c->ev_loop0, c->ev_loop1));
+  *ms_out = ms;
+  if (passes_out) *passes_out = c->loop_passes;
+  return FOT_OK;
+}
+
+fot_status fot_set_problem(fot_ctx* c, const float* g, const float* G) {
+  if (!c || bad_ptr(g) || bad_ptr(G)) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  FOT_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  set_problem_simt(c, g, G, nullptr, 0.f);
+  c->have_problem = true;
+  c->have_solution = false;
+  return check_launch(c);
+}
+
+static void half_step(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
+                      float* pot_out, float* logsum) {
+  if (c->precision == FOT_MIXED && c->tc)
+    half_step_tc(c, pot_in, lmarg, eps, pot_out, logsum);
+  else
+    half_step_simt(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
+}
+
+static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int units, int iters) {
+  const int64_t l0 = c->launches;
+  cudaEventRecord(c->ev_loop0, c->stream);
+  for (int t = 0; t < iters; ++t) {
+    const double e = eps_px(c, eps[n_eps == 1 ? 0 : t], units);
+    // Eq. 7: f = eps (log a - log(Lambda V Lambda)); keep S of the last u-update (Eqs. 9-10)
+    half_step(c, c->psi, c->la, e, c->f, t == iters - 1 ? c->S_last : nullptr);
+    // Eq. 8: psi = eps (log b - log(Lambda u Lambda))
+    half_step(c, c->f, c->lb, e, c->psi, nullptr);
+    c->eps_last = e;
+  }
+  cudaEventRecord(c->ev_loop1, c->stream);
+  c->loop_passes = c->launches - l0;
+  if (iters > 0) c->have_solution = true;
+  return check_launch(c);
+}
+
+fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,
+                     int n_eps, int eps_units, int iters) {
+  if (!c || bad_ptr(g) || bad_ptr(G)) return FOT_EINVAL;
+  fot_status s = check_eps(eps, n_eps, iters);
+  if (s != FOT_OK) return s;
+  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
+  if (!isfinite(dx)) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  FOT_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  const double n = (double)(c->rows > c->cols ? c->rows : c->cols);
+  c->dx = dx > 0.0 ? dx : 1.0 / sqrt(n);
+  // Algorithm 1 initialisation: V = 1/(rows cols)  ->  psi0 = eps_0 log(1/(rows cols))
+  const double e0 = eps_px(c, eps[0], eps_units);
+  const float psi0 = (float)(e0 * log(1.0 / ((double)c->rows * c->cols)));
+  set_problem_simt(c, g, G, c->psi, psi0);
+  c->have_problem = true;
+  c->have_solution = false;
+  return run_iterations(c, eps, n_eps, eps_units, iters);
+}
+
+fot_status fot_resume(fot_ctx* c, const double* eps, int n_eps, int eps_units, int iters) {
+  if (!c) return FOT_EINVAL;
+  if (!c->have_problem) return FOT_ESTATE;
+  fot_status s = check_eps(eps, n_eps, iters);
+  if (s != FOT_OK) return s;
+  FOT_CUDA(cudaSetDevice(c->device));
+  return run_iterations(c, eps, n_eps, eps_units, iters);
+}
+
+fot_status fot_sync(fot_ctx* c) {
+  if (!c) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  return read_latched(c);
+}
+
+fot_status fot_potentials(fot_ctx* c, float* f_out, float* psi_out) {
+  if (!c) return FOT_EINVAL;
+  if (!c->have_solution) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)c->rows * c->cols * sizeof(float);
+  if (f_out) FOT_CUDA(cudaMemcpyAsync(f_out, c->f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (psi_out) FOT_CUDA(cudaMemcpyAsync(psi_out, c->psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return read_latched(c);
+}
+
+fot_status fot_set_potentials(fot_ctx* c, const float* f, const float* psi) {
+  if (!c || bad_ptr(psi)) return FOT_EINVAL;
+  if (!c->have_problem) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)c->rows * c->cols * sizeof(float);
+  if (f) FOT_CUDA(cudaMemcpyAsync(c->f, f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  FOT_CUDA(cudaMemcpyAsync(c->psi, psi, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return FOT_OK;
+}
+
+fot_status fot_phase(fot_ctx* c, float* phi_out, float* dphidx_out, float* dphidy_out) {
+  if (!c) return FOT_EINVAL;
+  if (!c->have_solution) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  float* Dx = dphidx_out ? dphidx_out : c->tmp;
+  float* Dy = dphidy_out ? dphidy_out : c->tmp2;
+  moments_simt(c, c->eps_last, c->dx, Dx, Dy);
+  if (phi_out) integrate_phase(c, Dx, Dy, c->dx, phi_out);
+  fot_status s = check_launch(c);
+  if (s != FOT_OK) return s;
+  return read_latched(c);
+}
+
+fot_status fot_marginal_error(fot_ctx* c, double* l1_out, double* dual_out) {
+  if (!c || !l1_out) return FOT_EINVAL;
+  if (!c->have_solution) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  const double e = c->eps_last;
+  // exact FP32 evaluation of log(Lambda V Lambda) and log(Lambda u Lambda) on the stored
+  // potentials; tmp2 receives throw-away potentials
+  half_step_simt(c, c->psi, c->la, e, c->tmp2, c->tmp, c->R);    // tmp = S(psi)
+  half_step_simt(c, c->f, c->lb, e, c->tmp2, c->R2, c->R);       // R2 = T(f)
+  double* out = c->red + 4 * c->red_blocks;
+  marginal_stats(c, c->f, c->tmp, c->psi, c->R2, e, out);
+  double h[6];
+  FOT_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  fot_status s = read_latched(c);
+  if (s != FOT_OK) return s;
+  *l1_out = h[0] + h[3];
+  if (dual_out) *dual_out = h[2] + h[5] - e * h[1] + e;
+  return FOT_OK;
+}
+
+fot_status fot_u_update(fot_ctx* c, const float* psi_in, double eps, float* f_out,
+                        float* logsum_out) {
+  if (!c || bad_ptr(psi_in) || bad_ptr(f_out) || !(eps > 0.0) || !isfinite(eps)) return FOT_EINVAL;
+  if (!c->have_problem) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  half_step(c, psi_in, c->la, eps, f_out, logsum_out);
+  return check_launch(c);
+}
+
+fot_status fot_v_update(fot_ctx* c, const float* f_in, double eps, float* psi_out,
+                        float* logsum_out) {
+  if (!c || bad_ptr(f_in) || bad_ptr(psi_out) || !(eps > 0.0) || !isfinite(eps)) return FOT_EINVAL;
+  if (!c->have_problem) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  half_step(c, f_in, c->lb, eps, psi_out, logsum_out);
+  return check_launch(c);
+}
+
+fot_status fot_c_transform(fot_ctx* c, const float* pot_in, float* out) {
+  if (!c || bad_ptr(pot_in) || bad_ptr(out)) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  c_transform_envelope(c, pot_in, out);
+  return check_launch(c);
+}
+
+fot_status fot_solve_phase_host(fot_ctx* c, const float* g_host, const float* G_host, double dx,
+                                const double* eps, int n_eps, int eps_units, int iters,
+                                float* phi_host) {
+  if (!c || !g_host || !G_host || !phi_host) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  const size_t bytes = (size_t)c->rows * c->cols * sizeof(float);
+  // stage the inputs in context scratch that the solve does not touch before prep
+  FOT_CUDA(cudaMemcpyAsync(c->tmp, g_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  FOT_CUDA(cudaMemcpyAsync(c->tmp2, G_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  fot_status s = fot_solve(c, c->tmp, c->tmp2, dx, eps, n_eps, eps_units, iters);
+  if (s != FOT_OK) return s;
+  moments_simt(c, c->eps_last, c->dx, c->tmp, c->tmp2);
+  integrate_phase(c, c->tmp, c->tmp2, c->dx, c->phi);
+  s = check_launch(c);
+  if (s != FOT_OK) return s;
+  FOT_CUDA(cudaMemcpyAsync(phi_host, c->phi, bytes, cudaMemcpyDeviceToHost, c->stream));
+  return read_latched(c);
+}
+
+}  // extern "C"

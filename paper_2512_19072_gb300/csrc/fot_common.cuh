@@ -1,0 +1,67 @@
+// Shared device helpers and the context layout of the FOT library (internal header).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/fot.h"
+
+namespace fot {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// 2^x with the MUFU.EX2 unit (PTX ex2.approx.ftz.f32: relative error ~2^-22, results
+// below 2^-126 flush to zero, ex2(-inf) = 0).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Latch the first device-side error of a context (later errors are dropped).
+__device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ bool error_latched(const int* err) {
+  return *(volatile const int*)err != 0;
+}
+
+}  // namespace fot
+
+// Context (opaque to callers).  Every device buffer is owned here.
+struct fot_ctx {
+  int rows = 0, cols = 0, device = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  // device images, rows x cols unless noted
+  float* la = nullptr;       // log a (natural), -inf on zero mass
+  float* lb = nullptr;       // log b
+  float* f = nullptr;        // source potential, px^2
+  float* psi = nullptr;      // target potential, px^2
+  float* R = nullptr;        // axis-pass intermediate, transposed (cols x rows), log2 units
+  float* R2 = nullptr;       // second intermediate (moments / stats), cols x rows
+  float* S_last = nullptr;   // natural-log kernel sum of the last u-update (Eqs. 9-10)
+  float* tmp = nullptr;      // rows x cols scratch (stats, moments)
+  float* tmp2 = nullptr;     // rows x cols scratch
+  float* phi = nullptr;      // rows x cols phase (host-buffer entry point)
+  float* col_phi = nullptr;  // rows: phase along the centre column
+  double* red = nullptr;     // reduction scratch (partials + results)
+  int* err = nullptr;        // latched device status
+  int red_blocks = 0;
+  // host-side state
+  double dx = 0.0;
+  double eps_last = 0.0;
+  bool have_problem = false;
+  bool have_solution = false;
+  int64_t launches = 0;
+  // CUDA events bracketing the last Sinkhorn loop (only axis passes run inside it)
+  cudaEvent_t ev_loop0 = nullptr, ev_loop1 = nullptr;
+  int64_t loop_passes = 0;   // axis-pass launches inside the last loop
+  // mixed-precision (tensor-core) resources, owned by fot_tc.cu
+  void* tc = nullptr;
+};
+
+namespace fot {
+// Implemented in fot_api.cu
+cudaError_t launch_error_check(fot_ctx* c);
+}  // namespace fot

@@ -156,15 +156,17 @@ def _c3_shapes(n, rng, scale):
     return specs
 
 
-def _c3_render(n, specs, s):
+def _c3_render(n, specs, s, f=1.0):
+    """Render the shapes on an n x n grid with sizes times s; f rescales every length
+    (positions included) to render the same composite at another resolution."""
     out = np.zeros((n, n))
     for kind, p, cj, ck in specs:
         if kind == "rect":
-            img = rect(n, n, p[0] * s, p[1] * s, cj, ck)
+            img = rect(n, n, p[0] * s * f, p[1] * s * f, cj * f, ck * f)
         elif kind == "disk":
-            img = disk(n, n, p * s, cj, ck)
+            img = disk(n, n, p * s * f, cj * f, ck * f)
         else:
-            img = ring(n, n, p[0] * s, p[1] * s, cj, ck)
+            img = ring(n, n, p[0] * s * f, p[1] * s * f, cj * f, ck * f)
         out = np.maximum(out, img)
     return out
 
@@ -177,14 +179,23 @@ def config3(n=1024, iters=200, eps_paper=2e-4):
     scale = n / 256.0
     g = normalise_power(_two_gauss(n, rng, scale))
     specs = _c3_shapes(n, rng, scale)
+    nb = min(n, 256)                          # bisect the size factor on a coarse copy
     lo, hi = 0.2, 4.0
-    for _ in range(40):                       # bisect the global size factor to 30 % coverage
+    for _ in range(24):
         mid = 0.5 * (lo + hi)
-        cov = float((_c3_render(n, specs, mid) > 0).mean())
+        cov = float((_c3_render(nb, specs, mid, nb / n) > 0).mean())
         if cov < 0.30:
             lo = mid
         else:
             hi = mid
+    if nb < n:                                # refine at full resolution (edges are 2 px)
+        lo, hi = 0.5 * (lo + hi), 0.5 * (lo + hi) * 1.6
+        for _ in range(10):
+            mid = 0.5 * (lo + hi)
+            if float((_c3_render(n, specs, mid) > 0).mean()) < 0.30:
+                lo = mid
+            else:
+                hi = mid
     G = normalise_power(_c3_render(n, specs, 0.5 * (lo + hi)))
     eps = eps_paper * n * n
     return Workload(f"c3_{n}_twogauss_to_12shapes", g, G, np.full(iters, eps), iters,
