@@ -115,6 +115,13 @@ fot_status fot_set_potentials(fot_ctx* ctx, const float* f, const float* psi);
  * with dphidx, then along every row with dphidy.  Any output may be NULL.  Synchronising. */
 fot_status fot_phase(fot_ctx* ctx, float* phi_out, float* dphidx_out, float* dphidy_out);
 
+/* The same phase step from caller data: psi (target potential, px^2) and logsum_u (the
+ * natural-log kernel sum S = log(Lambda V Lambda) of the u-update, so that u/g^2 = e^-S),
+ * device rows x cols; eps in px^2; dx as in fot_solve (<= 0: 1/sqrt(n)).  Outputs as in
+ * fot_phase (any may be NULL).  Synchronising. */
+fot_status fot_moments(fot_ctx* ctx, const float* psi, const float* logsum_u, double eps,
+                       double dx, float* phi_out, float* dphidx_out, float* dphidy_out);
+
 /* Marginal violation of the current iterate, ||Gamma 1 - a||_1 + ||Gamma^T 1 - b||_1
  * (the total-variation convergence measure of Sec. 3, times two), from one extra exact
  * FP32 u-half-step evaluated on the stored potentials (never with the mixed-precision

@@ -45,6 +45,7 @@ _SIGS = {
     "fot_set_potentials": (_I, [_P, _P, _P]),
     "fot_phase": (_I, [_P, _P, _P, _P]),
     "fot_marginal_error": (_I, [_P, _DP, _DP]),
+    "fot_moments": (_I, [_P, _P, _P, _D, _D, _P, _P, _P]),
     "fot_u_update": (_I, [_P, _P, _D, _P, _P]),
     "fot_v_update": (_I, [_P, _P, _D, _P, _P]),
     "fot_c_transform": (_I, [_P, _P, _P]),
@@ -166,6 +167,14 @@ def fot_phase(ctx):
     ctx._sync_stream()
     _check(_lib.fot_phase(ctx._h, _ptr(phi), _ptr(dx), _ptr(dy)), "fot_phase")
     return phi, dx, dy
+
+
+def fot_moments(ctx, psi, logsum_u, eps, dx=0.0):
+    phi, Dx, Dy = ctx.empty(), ctx.empty(), ctx.empty()
+    ctx._sync_stream()
+    _check(_lib.fot_moments(ctx._h, _ptr(psi), _ptr(logsum_u), float(eps), float(dx), _ptr(phi),
+                            _ptr(Dx), _ptr(Dy)), "fot_moments")
+    return phi, Dx, Dy
 
 
 def fot_marginal_error(ctx):

@@ -12,7 +12,8 @@
 namespace fot {
 void half_step_simt(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                     float* pot_out, float* logsum, float* tmp);
-void moments_simt(fot_ctx* c, double eps, double dx, float* Dx, float* Dy);
+void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, double dx,
+                  float* Dx, float* Dy);
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
 void fill(fot_ctx* c, float* p, size_t N, float v);
 void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
@@ -261,8 +262,24 @@ fot_status fot_phase(fot_ctx* c, float* phi_out, float* dphidx_out, float* dphid
   FOT_CUDA(cudaSetDevice(c->device));
   float* Dx = dphidx_out ? dphidx_out : c->tmp;
   float* Dy = dphidy_out ? dphidy_out : c->tmp2;
-  moments_simt(c, c->eps_last, c->dx, Dx, Dy);
+  moments_simt(c, c->psi, c->S_last, c->eps_last, c->dx, Dx, Dy);
   if (phi_out) integrate_phase(c, Dx, Dy, c->dx, phi_out);
+  fot_status s = check_launch(c);
+  if (s != FOT_OK) return s;
+  return read_latched(c);
+}
+
+fot_status fot_moments(fot_ctx* c, const float* psi, const float* logsum_u, double eps, double dx,
+                       float* phi_out, float* dphidx_out, float* dphidy_out) {
+  if (!c || bad_ptr(psi) || bad_ptr(logsum_u) || !(eps > 0.0) || !isfinite(eps) || !isfinite(dx))
+    return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  const double n = (double)(c->rows > c->cols ? c->rows : c->cols);
+  const double h = dx > 0.0 ? dx : 1.0 / sqrt(n);
+  float* Dx = dphidx_out ? dphidx_out : c->tmp;
+  float* Dy = dphidy_out ? dphidy_out : c->tmp2;
+  moments_simt(c, psi, logsum_u, eps, h, Dx, Dy);
+  if (phi_out) integrate_phase(c, Dx, Dy, h, phi_out);
   fot_status s = check_launch(c);
   if (s != FOT_OK) return s;
   return read_latched(c);
@@ -324,7 +341,7 @@ fot_status fot_solve_phase_host(fot_ctx* c, const float* g_host, const float* G_
   FOT_CUDA(cudaMemcpyAsync(c->tmp2, G_host, bytes, cudaMemcpyHostToDevice, c->stream));
   fot_status s = fot_solve(c, c->tmp, c->tmp2, dx, eps, n_eps, eps_units, iters);
   if (s != FOT_OK) return s;
-  moments_simt(c, c->eps_last, c->dx, c->tmp, c->tmp2);
+  moments_simt(c, c->psi, c->S_last, c->eps_last, c->dx, c->tmp, c->tmp2);
   integrate_phase(c, c->tmp, c->tmp2, c->dx, c->phi);
   s = check_launch(c);
   if (s != FOT_OK) return s;

@@ -175,18 +175,19 @@ void half_step_simt(fot_ctx* c, const float* pot_in, const float* lmarg, double 
 }
 
 // Phase-gradient moments (Eqs. 9-10, ratio form with u/g^2 = exp(-S_last)).
-void moments_simt(fot_ctx* c, double eps, double dx, float* Dx, float* Dy) {
+void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, double dx,
+                  float* Dx, float* Dy) {
   const int rows = c->rows, cols = c->cols;
   // row pass with the final psi: log2 row sums Rf[k][L] and the conditional mean of Y_M
   PassArgs p = base_args(c, eps);
-  p.x = c->psi; p.x_scale = (float)(1.4426950408889634 / eps);
+  p.x = psi; p.x_scale = (float)(1.4426950408889634 / eps);
   p.n_rows = rows; p.len = cols; p.y = c->R; p.y2 = c->R2;
   p.coord0 = (float)(-(double)(cols / 2) / (cols * dx));
   p.coord_step = (float)(1.0 / (cols * dx));
   launch_pass<8, kLseMean>(c, p);
   // column pass: Dx = sum_L X_L w, Dy = sum_L E[Y|L,k] w, w = 2^(Rf - d^2 c2) / e^S_last
   PassArgs q = base_args(c, eps);
-  q.x = c->R; q.w = c->R2; q.off = c->S_last; q.x_scale = 1.f;
+  q.x = c->R; q.w = c->R2; q.off = S; q.x_scale = 1.f;
   q.n_rows = cols; q.len = rows; q.y = Dx; q.y2 = Dy;
   q.coord0 = (float)(-(double)(rows / 2) / (rows * dx));
   q.coord_step = (float)(1.0 / (rows * dx));

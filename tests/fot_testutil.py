@@ -7,6 +7,17 @@ import torch
 POT_RTOL = 1e-6
 
 
+def solve_rtol(iters):
+    """Normwise bound for potentials after `iters` full iterations in FP32.
+
+    Every half-step rounds the stored potential once (<= 2^-24 |pot|) and rounds the
+    potential/eps product it reads (<= 2^-24 |pot|/eps in the exponent, i.e. <= 2^-24 |pot|
+    after the update); the iteration neither amplifies nor (at small eps) noticeably damps
+    these, so they add like a random walk over the 2 * iters half-steps.  Bound: a safety
+    factor 4 on sqrt(2 iters) * 2 * 2^-24, and never below the single-step bound."""
+    return max(POT_RTOL, 4.0 * (2.0 * iters) ** 0.5 * 2.0 * 2.0 ** -24)
+
+
 def f32(a):
     """Round an FP64 array to FP32 and back: the exact values the GPU receives."""
     return np.asarray(a, dtype=np.float32).astype(np.float64)
