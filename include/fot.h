@@ -139,6 +139,31 @@ fot_status fot_u_update(fot_ctx* ctx, const float* psi_in, double eps, float* f_
 fot_status fot_v_update(fot_ctx* ctx, const float* f_in, double eps, float* psi_out,
                         float* logsum_out);
 
+/* Allocation-free u-update.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory once they are running, for example a
+ * real-time hologram loop that reserves all of its memory at start-up because cudaMalloc
+ * can synchronise the device and stall the loop, or a plug-in whose host owns every
+ * device allocation through its own allocator.  It computes the same update as
+ * fot_u_update, f = eps (log_a - S) with S = log(Lambda exp(psi/eps) Lambda) (Eq. 7), but
+ * needs no fot_ctx: the caller passes every input and output (device, rows x cols float32:
+ * psi_in in px^2, log_a = natural log of the normalised source marginal a = g^2/sum g^2,
+ * -INFINITY where a = 0; f_out; logsum_out may be NULL), and the intermediate lives in a
+ * static device array of FOT_NOALLOC_MAX_PIXELS floats (4 MiB) that every GPU loading this
+ * library holds until the process exits.  Nothing is allocated: no cudaMalloc, no cudaFree,
+ * no allocating library call.
+ *  - rows * cols > FOT_NOALLOC_MAX_PIXELS, or rows / cols outside [1, 4096]: FOT_EINVAL.
+ *  - Runs on the current device, enqueued on cuda_stream (NULL = legacy default stream);
+ *    asynchronous.  Non-finite results show up as non-finite values in f_out.
+ *  - The first call on a device looks up the static array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any
+ *    stream capture begins.  The host-side cache of that address is not thread-safe for a
+ *    device's first call.
+ *  - Every call shares the one array and it keeps the last call's contents: calls whose
+ *    work overlaps on the GPU (different streams, or different host threads) race on it. */
+#define FOT_NOALLOC_MAX_PIXELS (1024 * 1024)
+fot_status fot_u_update_noalloc(const float* psi_in, const float* log_a, int rows, int cols,
+                                double eps, float* f_out, float* logsum_out, void* cuda_stream);
+
 /* Exact c-transform, the eps -> 0 limit of a half-step (the log a term vanishes):
  *   out_jk = min_LM [ ((j-L)^2 + (k-M)^2)/2 - pot_LM ],
  * by a lower envelope of parabolas along each row, then along each column.  -INFINITY

@@ -49,6 +49,7 @@ _SIGS = {
     "fot_u_update": (_I, [_P, _P, _D, _P, _P]),
     "fot_v_update": (_I, [_P, _P, _D, _P, _P]),
     "fot_c_transform": (_I, [_P, _P, _P]),
+    "fot_u_update_noalloc": (_I, [_P, _P, _I, _I, _D, _P, _P, _P]),
     "fot_solve_phase_host": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _P]),
     "fot_launch_count": (ctypes.c_int64, [_P]),
     "fot_loop_time": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
@@ -199,6 +200,17 @@ def fot_v_update(ctx, f, eps, with_logsum=False):
     ctx._sync_stream()
     _check(_lib.fot_v_update(ctx._h, _ptr(f), float(eps), _ptr(psi), _ptr(T)), "fot_v_update")
     return (psi, T) if with_logsum else psi
+
+
+def fot_u_update_noalloc(psi, log_a, eps, f_out=None, logsum_out=None):
+    """Allocation-free u-update on the current device and stream (no context): the caller
+    supplies psi, log_a and the outputs (torch tensors, rows x cols float32)."""
+    rows, cols = psi.shape
+    if f_out is None:
+        f_out = torch.empty_like(psi)
+    _check(_lib.fot_u_update_noalloc(_ptr(psi), _ptr(log_a), rows, cols, float(eps), _ptr(f_out),
+                                     _ptr(logsum_out), _stream()), "fot_u_update_noalloc")
+    return f_out
 
 
 def fot_c_transform(ctx, pot):

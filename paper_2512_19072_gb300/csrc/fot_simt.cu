@@ -416,3 +416,72 @@ void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, fl
 }
 
 }  // namespace fot
+
+// ------------------------------------------------------------------------------------
+// Allocation-free u-update (fot_u_update_noalloc in include/fot.h).
+//
+// For callers that may not allocate device memory at call time: it runs the same two
+// axis passes as fot_u_update, but its intermediate lives in the file-scope device array
+// below instead of context-owned cudaMalloc memory.  Every GPU that loads this library
+// keeps these FOT_NOALLOC_MAX_PIXELS floats (4 MiB) until the process exits.  All calls
+// share the array, so calls whose work overlaps on the GPU race on it.
+// ------------------------------------------------------------------------------------
+static __device__ __align__(256) float g_noalloc_scratch[FOT_NOALLOC_MAX_PIXELS];
+static __device__ int g_noalloc_err;   // error word the passes latch into; cleared per call
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+struct NoallocDevice {
+  float* scratch = nullptr;   // device address of g_noalloc_scratch on this device
+  int* err = nullptr;         // device address of g_noalloc_err on this device
+  bool ready = false;
+};
+NoallocDevice g_noalloc_devices[kNoallocMaxDevices];
+
+template <int RB, int MODE>
+cudaError_t launch_pass_noalloc(const fot::PassArgs& p, cudaStream_t s) {
+  const int threads = std::min(256, ((p.len + 31) / 32) * 32);
+  dim3 grid((p.len + threads - 1) / threads, (p.n_rows + RB - 1) / RB);
+  const size_t smem = (size_t)p.len * RB * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(fot::axis_pass_kernel<RB, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  fot::axis_pass_kernel<RB, MODE><<<grid, threads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+extern "C" fot_status fot_u_update_noalloc(const float* psi_in, const float* log_a, int rows,
+                                           int cols, double eps, float* f_out,
+                                           float* logsum_out, void* cuda_stream) {
+  if (!psi_in || !log_a || !f_out) return FOT_EINVAL;
+  if (rows < 1 || cols < 1 || rows > 4096 || cols > 4096) return FOT_EINVAL;
+  if ((size_t)rows * (size_t)cols > (size_t)FOT_NOALLOC_MAX_PIXELS) return FOT_EINVAL;
+  if (!(eps > 0.0) || !isfinite(eps)) return FOT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FOT_ECUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return FOT_EUNSUPPORTED;
+  NoallocDevice& d = g_noalloc_devices[dev];
+  if (!d.ready) {
+    // one-time set-up on this device (current): the symbols' device addresses
+    if (cudaGetSymbolAddress((void**)&d.scratch, g_noalloc_scratch) != cudaSuccess) return FOT_ECUDA;
+    if (cudaGetSymbolAddress((void**)&d.err, g_noalloc_err) != cudaSuccess) return FOT_ECUDA;
+    d.ready = true;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (cudaMemsetAsync(d.err, 0, sizeof(int), s) != cudaSuccess) return FOT_ECUDA;
+  fot::PassArgs p{};
+  p.err = d.err;
+  p.c2 = (float)(1.4426950408889634 / (2.0 * eps));
+  p.eps = (float)eps;
+  fot::PassArgs q = p;
+  // pass over the contiguous axis into the static scratch, written [k][L]
+  p.x = psi_in; p.x_scale = (float)(1.4426950408889634 / eps);
+  p.n_rows = rows; p.len = cols; p.y = d.scratch;
+  if (launch_pass_noalloc<8, fot::kLse>(p, s) != cudaSuccess) return FOT_ECUDA;
+  // pass over the row axis with the fused update f = eps (log a - S), written [j][k]
+  q.x = d.scratch; q.x_scale = 1.f; q.n_rows = cols; q.len = rows;
+  q.y = f_out; q.lmarg = log_a; q.logsum = logsum_out;
+  if (launch_pass_noalloc<8, fot::kLsePot>(q, s) != cudaSuccess) return FOT_ECUDA;
+  return FOT_OK;
+}
