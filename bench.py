@@ -37,7 +37,7 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fot", choices=["fot", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "mixed"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32_dense", "mixed"])
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -163,10 +163,12 @@ def _peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-# MUFU ex2 issue rate used as the ALU roofline of the exact FP32 pass: 32 ex2 per clock
-# per SM on sm_103 (GB300 doubles the sm_100 special-function rate for exponentials),
-# times 152 SMs and the maximum SM clock.
+# ALU rooflines (per SM per clock, times 152 SMs and the maximum SM clock):
+#  - MUFU ex2: 32 lanes/clk/SM on sm_103 (GB300 doubles sm_100's special-function rate;
+#    ncu's sm__inst_executed_pipe_xu peak agrees), bound of the dense exact pass;
+#  - FP32 FFMA: 128 lanes/clk/SM = 256 flop/clk/SM, bound of the banded pass's GEMM loop.
 EX2_PER_CLK_PER_SM = 32
+FFMA_FLOP_PER_CLK_PER_SM = 256
 N_SM = 152
 
 
@@ -185,7 +187,7 @@ def run_gpu(a):
     g = torch.from_numpy(w.g.astype(np.float32)).cuda()
     G = torch.from_numpy(w.G.astype(np.float32)).cuda()
     eps = w.eps
-    prec = B.FOT_MIXED if a.precision == "mixed" else B.FOT_FP32
+    prec = {"fp32": B.FOT_FP32, "fp32_dense": B.FOT_FP32_DENSE, "mixed": B.FOT_MIXED}[a.precision]
     ctx = B.fot_create(n, n, prec)
     phi = ctx.empty()
     Dx = ctx.empty()
@@ -206,6 +208,8 @@ def run_gpu(a):
     torch.cuda.synchronize()
     clocks = _Clocks(dev)
     l0 = B.fot_launch_count(ctx)
+    w0, wt0 = B.fot_work_count(ctx, tensor=True)
+    torch.cuda.synchronize()
     evs = []
     loop_ms = []
     passes = 0
@@ -224,6 +228,9 @@ def run_gpu(a):
         dist.barrier()
     torch.cuda.synchronize()
     launches = B.fot_launch_count(ctx) - l0
+    w1, wt1 = B.fot_work_count(ctx, tensor=True)
+    terms_per_step = (w1 - w0) / a.steps
+    tensor_terms_per_step = (wt1 - wt0) / a.steps
     clk = clocks.stop()
     step_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
     if ws > 1:
@@ -235,19 +242,47 @@ def run_gpu(a):
     line = None
     if rank == 0:
         l1, dual = B.fot_marginal_error(ctx)
-        # roofline of the dominant kernel (the axis pass; only axis passes run in the loop)
-        pass_ms = statistics.median(loop_ms) / max(passes, 1)
+        # roofline of the dominant kernel group: the Sinkhorn loop runs only axis passes (and,
+        # for the banded form, their chunk-maximum pre-pass); its time over the terms evaluated
+        loop = statistics.median(loop_ms)
+        loop_terms = terms_per_step - 0.0
         peaks, peak_src = _peaks()
         clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        ex2_per_pass = float(n) * n * n                   # one exponential per (row, out, term)
-        achieved = ex2_per_pass / (pass_ms * 1e-3) / 1e12  # Tex2/s
-        peak = EX2_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "axis_pass_kernel (exact FP32 log-sum-exp axis pass)",
-                "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz "
-                               f"(max SM clock, {peak_src} peaks file)",
-                "pass_ms": pass_ms}
+        dense_terms = 4.0 * a.iters * n * n * n           # every (row, output, term) of 4n passes
+        if a.precision == "mixed":
+            # tensor pipe: each window term is three BF16 multiply-adds (split precision)
+            peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+            achieved = 6.0 * tensor_terms_per_step / (loop * 1e-3) / 1e12
+            loop_terms = terms_per_step - 2.0 * n * n * n
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "kernel": "tc_pass_kernel (tcgen05 split-BF16 window GEMM) + banded CUDA-core tail",
+                    "peak_source": "cuBLAS bf16 sustained (MEASURED_PEAKS.json)",
+                    "tensor_share_of_terms": tensor_terms_per_step / max(loop_terms, 1.0),
+                    "executed_terms_per_iter": loop_terms / a.iters,
+                    "dense_terms_per_iter": dense_terms / a.iters,
+                    "dense_equivalent_tflops": 2.0 * dense_terms / (loop * 1e-3) / 1e12}
+        elif a.precision == "fp32_dense":
+            achieved = dense_terms / (loop * 1e-3) / 1e12  # Tex2/s: one exponential per term
+            peak = EX2_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
+                    "kernel": "axis_pass_kernel (dense exact FP32 log-sum-exp pass)",
+                    "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz"}
+        else:
+            # executed multiply-adds of the window GEMMs (2 flop per term); the loop of one
+            # step evaluates the 200 iterations' terms (the phase step is outside the loop)
+            loop_terms = terms_per_step - 2.0 * n * n * n   # phase: two dense moment passes
+            achieved = 2.0 * loop_terms / (loop * 1e-3) / 1e12
+            peak = FFMA_FLOP_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "kernel": "band_pass_kernel + chunk_max_kernel (banded FP32 axis passes)",
+                    "peak_source": f"FP32 FFMA {FFMA_FLOP_PER_CLK_PER_SM} flop/clk/SM x {N_SM} SMs x "
+                                   f"{clk_mhz:.0f} MHz",
+                    "executed_terms_per_iter": loop_terms / a.iters,
+                    "dense_terms_per_iter": dense_terms / a.iters,
+                    "dense_equivalent_tflops": 2.0 * dense_terms / (loop * 1e-3) / 1e12}
+        roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None,
+                     "loop_ms": loop, "pass_ms": loop / max(passes, 1),
+                     "peak_file": peak_src})
         # end to end through the C ABI with host buffers (H2D of g, G and D2H of phi per step)
         gh = torch.from_numpy(w.g.astype(np.float32)).pin_memory()
         Gh = torch.from_numpy(w.G.astype(np.float32)).pin_memory()
@@ -267,7 +302,7 @@ def run_gpu(a):
         line = {"metric": METRIC, "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if a.precision == "fp32" else "bf16+f32",
+                "dtype": "bf16+f32" if a.precision == "mixed" else "f32",
                 "data": "synthetic (seeded two-Gaussian beam -> 12-shape composite target)",
                 "config": {"workload": w.name, "n": n, "iters_per_solve": a.iters,
                            "eps_px2": float(eps[0]), "eps_paper": 2e-4,

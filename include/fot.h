@@ -55,11 +55,15 @@ typedef enum {
 } fot_status;
 
 typedef enum {
-  FOT_FP32 = 0,          /* exact log-sum-exp axis passes, FP32 on the CUDA cores */
-  FOT_MIXED = 1          /* axis GEMMs on tcgen05 tensor cores (BF16 operands, FP32
-                            accumulation) with FP32 log-domain potentials; falls back
-                            per output to the exact FP32 pass where the offsets leave
-                            the BF16 exponent range */
+  FOT_FP32 = 0,          /* FP32 on the CUDA cores, banded: every output sums only the terms
+                            within 2^-40 of its largest (a provable window per 32-output
+                            tile); for large eps the window sum is a tilted FP32 GEMM with
+                            per-row max-offsets, for small eps an exact windowed
+                            log-sum-exp */
+  FOT_MIXED = 1,         /* the banded GEMM on tcgen05 tensor cores (split-BF16 operands,
+                            FP32 accumulation in TMEM) with FP32 log-domain potentials */
+  FOT_FP32_DENSE = 2     /* FP32 on the CUDA cores, every output scans every term with its
+                            own exact maximum (one exponential per term): the plain form */
 } fot_precision;
 
 typedef enum { FOT_EPS_PX2 = 0, FOT_EPS_PAPER = 1 } fot_eps_units;
@@ -184,6 +188,13 @@ int64_t fot_launch_count(const fot_ctx* ctx);
  * on the FP32 path).  Only axis passes run inside that loop, so ms / passes is their mean
  * duration.  Synchronises with the end of the loop. */
 fot_status fot_loop_time(fot_ctx* ctx, double* ms_out, int64_t* passes_out);
+
+/* Number of (row, output, summation index) terms the axis passes of this context have
+ * evaluated since creation: rows*len*len per dense pass, the window sizes for banded passes
+ * (each term is one multiply-add of the exp-domain contraction); tensor_terms_out (may be
+ * NULL) receives the part computed on the tensor cores (each term there is three BF16
+ * multiply-adds of the split-precision product).  Synchronising. */
+fot_status fot_work_count(fot_ctx* ctx, int64_t* terms_out, int64_t* tensor_terms_out);
 
 const char* fot_status_string(fot_status s);
 

@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-FOT_FP32, FOT_MIXED = 0, 1
+FOT_FP32, FOT_MIXED, FOT_FP32_DENSE = 0, 1, 2
 FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
 STATUS = {0: "FOT_OK", 1: "FOT_EINVAL", 2: "FOT_ENOMEM", 3: "FOT_ECUDA", 4: "FOT_ENONFINITE",
           5: "FOT_ETIMEOUT", 6: "FOT_EMASS", 7: "FOT_EUNSUPPORTED", 8: "FOT_ESTATE"}
@@ -53,6 +53,7 @@ _SIGS = {
     "fot_solve_phase_host": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _P]),
     "fot_launch_count": (ctypes.c_int64, [_P]),
     "fot_loop_time": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
+    "fot_work_count": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "fot_status_string": (ctypes.c_char_p, [_I]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -247,6 +248,12 @@ def fot_loop_time(ctx):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     _check(_lib.fot_loop_time(ctx._h, ctypes.byref(ms), ctypes.byref(n)), "fot_loop_time")
     return ms.value, n.value
+
+
+def fot_work_count(ctx, tensor=False):
+    n, t = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.fot_work_count(ctx._h, ctypes.byref(n), ctypes.byref(t)), "fot_work_count")
+    return (n.value, t.value) if tensor else n.value
 
 
 def exported_symbols():

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fot_common.cuh"
@@ -20,12 +21,15 @@ void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi
                     const float* T, double eps, double* out);
 void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, float* phi);
 void c_transform_envelope(fot_ctx* c, const float* pot_in, float* out);
+void half_step_band(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
+                    float* pot_out, float* logsum, float* tmp, float* cmax);
 // tensor-core path (fot_tc.cu)
 bool tc_supported(int rows, int cols);
 int tc_create(fot_ctx* c);
 void tc_destroy(fot_ctx* c);
 void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                   float* pot_out, float* logsum);
+int64_t tc_terms(fot_ctx* c);
 }  // namespace fot
 
 using namespace fot;
@@ -90,7 +94,8 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   if (!out) return FOT_EINVAL;
   *out = nullptr;
   if (rows < 1 || cols < 1 || rows > kMaxDim || cols > kMaxDim) return FOT_EINVAL;
-  if (precision != FOT_FP32 && precision != FOT_MIXED) return FOT_EINVAL;
+  if (precision != FOT_FP32 && precision != FOT_MIXED && precision != FOT_FP32_DENSE)
+    return FOT_EINVAL;
   if (getenv("FOT_FAULT_INJECT_ENOMEM")) return FOT_ENOMEM;   // host-side fault injection
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FOT_EINVAL;
@@ -110,8 +115,15 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   bool ok = true;
   for (float** b : bufs) ok = ok && cudaMalloc((void**)b, N * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->col_phi, (size_t)rows * sizeof(float)) == cudaSuccess;
+  // chunk maxima of both passes' inputs (32-wide chunks), then the per-(row, 16-output tile)
+  // plan of the larger pass (3 words each)
+  const size_t plan_words = 3 * std::max((size_t)rows * ((cols + 15) / 16), (size_t)cols * ((rows + 15) / 16));
+  const size_t nchunk = (size_t)rows * ((cols + 31) / 32) + (size_t)cols * ((rows + 31) / 32) + plan_words;
+  ok = ok && cudaMalloc((void**)&c->cmax, nchunk * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->red, (size_t)(4 * c->red_blocks + 16) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->terms, sizeof(unsigned long long)) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(c->terms, 0, sizeof(unsigned long long), c->stream) == cudaSuccess;
   if (ok) ok = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) == cudaSuccess;
   if (ok) ok = cudaEventCreate(&c->ev_loop0) == cudaSuccess && cudaEventCreate(&c->ev_loop1) == cudaSuccess;
   if (ok && precision == FOT_MIXED) {
@@ -136,11 +148,12 @@ void fot_destroy(fot_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->tc) tc_destroy(c);
   float* bufs[] = {c->la, c->lb, c->f, c->psi, c->R, c->R2, c->S_last, c->tmp, c->tmp2, c->phi,
-                   c->col_phi};
+                   c->col_phi, c->cmax};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (c->red) cudaFree(c->red);
   if (c->err) cudaFree(c->err);
+  if (c->terms) cudaFree(c->terms);
   if (c->ev_loop0) cudaEventDestroy(c->ev_loop0);
   if (c->ev_loop1) cudaEventDestroy(c->ev_loop1);
   delete c;
@@ -153,6 +166,18 @@ fot_status fot_set_stream(fot_ctx* c, void* s) {
 }
 
 int64_t fot_launch_count(const fot_ctx* c) { return c ? c->launches : -1; }
+
+fot_status fot_work_count(fot_ctx* c, int64_t* terms_out, int64_t* tensor_terms_out) {
+  if (!c || !terms_out) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  unsigned long long t = 0;
+  FOT_CUDA(cudaMemcpyAsync(&t, c->terms, sizeof(t), cudaMemcpyDeviceToHost, c->stream));
+  FOT_CUDA(cudaStreamSynchronize(c->stream));
+  const int64_t tt = c->tc ? tc_terms(c) : 0;
+  *terms_out = (int64_t)t + c->host_terms + tt;
+  if (tensor_terms_out) *tensor_terms_out = tt;
+  return FOT_OK;
+}
 
 fot_status fot_loop_time(fot_ctx* c, double* ms_out, int64_t* passes_out) {
   if (!c || !ms_out) return FOT_EINVAL;
@@ -180,8 +205,10 @@ static void half_step(fot_ctx* c, const float* pot_in, const float* lmarg, doubl
                       float* pot_out, float* logsum) {
   if (c->precision == FOT_MIXED && c->tc)
     half_step_tc(c, pot_in, lmarg, eps, pot_out, logsum);
-  else
+  else if (c->precision == FOT_FP32_DENSE)
     half_step_simt(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
+  else
+    half_step_band(c, pot_in, lmarg, eps, pot_out, logsum, c->R, c->cmax);
 }
 
 static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int units, int iters) {

@@ -45,8 +45,11 @@ struct fot_ctx {
   float* tmp2 = nullptr;     // rows x cols scratch
   float* phi = nullptr;      // rows x cols phase (host-buffer entry point)
   float* col_phi = nullptr;  // rows: phase along the centre column
+  float* cmax = nullptr;     // chunk maxima of a banded pass's input (rows*cols/32 + slack)
   double* red = nullptr;     // reduction scratch (partials + results)
   int* err = nullptr;        // latched device status
+  unsigned long long* terms = nullptr;  // device counter of evaluated (row, output, m) terms
+  int64_t host_terms = 0;    // terms of passes whose count is known on the host (dense)
   int red_blocks = 0;
   // host-side state
   double dx = 0.0;

@@ -148,6 +148,7 @@ static void launch_pass(fot_ctx* c, const PassArgs& p) {
   }
   axis_pass_kernel<RB, MODE><<<grid, threads, smem, c->stream>>>(p);
   c->launches++;
+  c->host_terms += (int64_t)p.n_rows * p.len * p.len;
 }
 
 static PassArgs base_args(fot_ctx* c, double eps) {

@@ -1,11 +1,414 @@
-// Tensor-core (tcgen05) axis passes: not available in this build yet.
-#include "fot_common.cuh"
+// Tensor-core (tcgen05) form of the banded axis pass.
+//
+// The window sums of the banded pass (fot_band.cu, steps 3-4) are a GEMM:
+//     C[r][kap] = sum_{m' < W} A[r][m'] B[m'][kap],
+//     A[r][m'] = 2^(x_r[lo_r + m'] - (kc - lo_r - m')^2 c - alpha_r)   (<= 1, per row)
+//     B[m'][kap] = 2^(2 kap (m' - W/2) c - kap^2 c)                     (same for all rows)
+// after which y[kc + kap][r] = alpha_r + 2 kap (lo_r + W/2 - kc) c + log2 C[r][kap] (the
+// per-row max-offsets of Sec. 3.1's Toeplitz contraction, plus the tilt).  One CTA computes
+// a 128-row x 16-output tile with tcgen05.mma (M = 128, N = 16, K = 16 per instruction), the
+// FP32 accumulator in tensor memory.  The operands are generated in shared memory by all
+// 256 threads (one exponential per element) in the canonical no-swizzle K-major layout,
+// double-buffered against the MMAs through mbarriers that tcgen05.commit arrives on.
+//
+// Precision: each operand is split into two BF16 parts, v = hi + lo (hi = bf16(v),
+// lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
+// about 2^-16 relative per product instead of 2^-8, FP32 accumulation.
+//
+// A CTA takes its tile only when the tilt bounds of the banded pass hold for the common
+// window length W of its 128 rows; otherwise it leaves a flag at 0 and the CUDA-core
+// banded kernels compute those rows.  Every mbarrier wait is bounded: on time-out the kernel
+// latches FOT_ETIMEOUT, stops issuing, frees its tensor memory and returns.
+#include "fot_band.cuh"
+
+#include <cuda_bf16.h>
+
+#include <new>
 
 namespace fot {
 
-bool tc_supported(int, int) { return false; }
-int tc_create(fot_ctx*) { return 1; }
-void tc_destroy(fot_ctx*) {}
-void half_step_tc(fot_ctx*, const float*, const float*, double, float*, float*) {}
+namespace {
+
+constexpr int kTM = 128;            // rows per CTA (MMA M, TMEM lanes)
+constexpr int kTN = 16;             // outputs per CTA (MMA N)
+constexpr int kKC = 64;             // window positions per pipeline stage
+constexpr int kThreads = 256;
+constexpr float kTiltMaxTC = 40.f;
+constexpr uint32_t kTmemCols = 32;  // FP32 accumulator columns (minimum allocation; kTN used)
+constexpr int kSpin = 1 << 20;      // bounded mbarrier polls
+
+// shared-memory layout of one stage (bytes): A_hi, A_lo (128 x 64 bf16 each), B_hi, B_lo
+// (16 x 64 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 1024 + kg * 128.
+constexpr int kABytes = kTM * kKC * 2;   // 16384
+constexpr int kBBytes = kTN * kKC * 2;   // 2048
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+constexpr int kSmemBytes = 2 * kStageBytes + 1024;   // 2 stages + barriers/params + slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major:
+// start address, leading (K-direction core-matrix) byte offset, stride (M/N-direction
+// 8-row group) byte offset, fixed version bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+      :: "r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false (and FOT_ETIMEOUT latched) if the phase never completes
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int* err) {
+  for (int i = 0; i < kSpin; ++i)
+    if (mbar_try(mbar, parity)) return true;
+  raise_error(err, FOT_ETIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // .x = a (low half), .y = b
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// split 8 consecutive values into hi / lo BF16 parts and store one 16-byte row of a core
+// matrix for each
+__device__ __forceinline__ void store_split8(const float* v, uint32_t hi_addr, uint32_t lo_addr) {
+  float h[8], l[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+    l[i] = v[i] - h[i];
+  }
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(hi_addr),
+               "r"(pack_bf16(h[0], h[1])), "r"(pack_bf16(h[2], h[3])), "r"(pack_bf16(h[4], h[5])),
+               "r"(pack_bf16(h[6], h[7])) : "memory");
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(lo_addr),
+               "r"(pack_bf16(l[0], l[1])), "r"(pack_bf16(l[2], l[3])), "r"(pack_bf16(l[4], l[5])),
+               "r"(pack_bf16(l[6], l[7])) : "memory");
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(BandArgs a, const float* __restrict__ p_alpha,
+                                                              const int* __restrict__ p_lo,
+                                                              const int* __restrict__ p_wl,
+                                                              unsigned char* __restrict__ done,
+                                                              unsigned long long* tc_terms) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ float s_alpha[kTM];
+  __shared__ int s_lo[kTM];
+  __shared__ int s_wmax;
+  if (error_latched(a.err)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int blk = blockIdx.y, tile = blockIdx.x;
+  const int r0 = blk * kTM;
+  const int k0 = tile * kTN, kc = k0 + kTN / 2;
+  const int k1 = min(k0 + kTN, a.len) - 1;
+  const float c = a.c, sc = a.x_scale;
+
+  // per-row plan and the common window length
+  if (tid == 0) s_wmax = 0;
+  __syncthreads();
+  if (tid < kTM) {
+    const int r = r0 + tid;
+    float al = -INFINITY;
+    int lo = 0, wl = 0;
+    if (r < a.n_rows) {
+      const size_t pi = (size_t)r * a.n_tiles + tile;
+      al = p_alpha[pi];
+      lo = p_lo[pi];
+      wl = p_wl[pi];
+    }
+    s_alpha[tid] = al;
+    s_lo[tid] = lo;
+    atomicMax(&s_wmax, wl);
+  }
+  __syncthreads();
+  const int W = ((s_wmax + kKC - 1) / kKC) * kKC;
+  const float kmax = (float)(kTN / 2);
+  const bool take = s_wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
+  if (tid == 0) done[(size_t)blk * a.n_tiles + tile] = take ? 1 : 0;
+  if (!take) return;                                    // CTA-uniform
+  if (tid == 0) atomicAdd(tc_terms, (unsigned long long)W * kTN * kTM);
+
+  // tensor memory for the 128 x 32 FP32 accumulator, and the two stage barriers
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_base_sh;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t idesc = instr_desc(kTM, kTN);
+  const float halfW = 0.5f * (float)W;
+  bool ok = true;
+
+  // producer roles: A row r = tid % 128, half h = tid / 128 (32 window positions each);
+  // B (threads 0..127): output n = tid % 16, positions (tid / 16) * 8 .. + 8
+  const int ar = tid & (kTM - 1), ah = tid >> 7;
+  const float a_alpha = s_alpha[ar];
+  const int a_lo = s_lo[ar];
+  const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
+  const int bn = tid & (kTN - 1), bq = (tid >> 4) & 7;
+  const float bkap = (float)(bn - kTN / 2);
+  const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
+
+  const int nchunk = W / kKC;
+  int issued = 0;                           // chunks whose MMAs were issued and committed
+  for (int ch = 0; ch < nchunk && ok; ++ch) {
+    const int s = ch & 1;
+    if (ch >= 2) {
+      ok = mbar_wait(smem_u32(&mbar[s]), ((ch - 2) >> 1) & 1, a.err);   // stage free again
+      ok = __syncthreads_and(ok);           // one decision for the whole CTA
+    }
+    if (!ok) break;
+    const uint32_t st = sbase + s * kStageBytes;
+    const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
+    const int m0 = ch * kKC;
+    // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int mp = m0 + ah * 32 + g * 8 + i;         // window position
+        const int m = a_lo + mp;
+        float e = 0.f;
+        if (a_alpha != -INFINITY && m < a.len) {
+          const float d = (float)(kc - m);
+          e = ex2(fmaf(-d * d, c, xr[m] * sc) - a_alpha);
+        }
+        v[i] = e;
+      }
+      const int kg = ah * 4 + g;                          // core-matrix column in the stage
+      const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
+      store_split8(v, sAhi + off, sAlo + off);
+    }
+    // B: 8 window positions of output bn
+    if (tid < kTN * 8) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float mp = (float)(m0 + bq * 8 + i) - halfW;
+        v[i] = ex2(fmaf(bt2, mp, btk));
+      }
+      const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
+      store_split8(v, sBhi + off, sBlo + off);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < kKC / 16; ++ks) {
+        const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, 1024);
+        const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, 1024);
+        const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, 1024);
+        const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, 1024);
+        mma_bf16(tmem_d, dAh, dBh, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+        mma_bf16(tmem_d, dAh, dBl, idesc, 1u);
+        mma_bf16(tmem_d, dAl, dBh, idesc, 1u);
+      }
+      mma_commit(smem_u32(&mbar[s]));
+    }
+    issued = ch + 1;
+  }
+  // all MMAs done: the last commit of each used stage
+  // (after a time-out the same bounded waits give in-flight MMAs a last chance to finish
+  // before the tensor memory is released)
+  bool ok_end = true;
+  if (issued >= 1)
+    ok_end = mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, a.err);
+  if (issued >= 2)
+    ok_end = mbar_wait(smem_u32(&mbar[(issued - 2) & 1]), ((issued - 2) >> 1) & 1, a.err) && ok_end;
+  ok = __syncthreads_and(ok && ok_end);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (ok && warp < 4) {
+    // accumulator row = TMEM lane = 32 * warp + lane, columns = the 16 outputs
+    uint32_t acc[kTN];
+    const uint32_t taddr = tmem_d + ((uint32_t)(32 * warp) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
+          "=r"(acc[6]), "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]),
+          "=r"(acc[12]), "=r"(acc[13]), "=r"(acc[14]), "=r"(acc[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int rloc = 32 * warp + lane;
+    const int r = r0 + rloc;
+    const float al = s_alpha[rloc];
+    const float mref = (float)s_lo[rloc] + halfW;
+    if (r < a.n_rows) {
+#pragma unroll
+      for (int n = 0; n < kTN; ++n) {
+        const int k = k0 + n;
+        if (k > k1) break;
+        const float kap = (float)(n - kTN / 2);
+        const float cv = __uint_as_float(acc[n]);
+        float out = -INFINITY;
+        if (al != -INFINITY) {
+          if (cv > 0.f && isfinite(cv))
+            out = al + 2.f * kap * (mref - (float)kc) * c + log2f(cv);
+          else
+            raise_error(a.err, FOT_ENONFINITE);
+        }
+        const size_t yi = (size_t)k * a.n_rows + r;
+        if (MODE == 0) {
+          a.y[yi] = out;
+        } else {
+          const float sv = out * kLn2;
+          const float lm = a.lmarg[yi];
+          float pot;
+          if (lm == -INFINITY) {
+            pot = -INFINITY;
+          } else {
+            pot = a.eps * (lm - sv);
+            if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
+          }
+          a.y[yi] = pot;
+          if (a.logsum) a.logsum[yi] = sv;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(kTmemCols)
+                 : "memory");
+}
+
+struct TcState {
+  unsigned char* done = nullptr;          // per (128-row block, tile): taken by the tensor kernel
+  unsigned long long* tc_terms = nullptr; // window terms computed on the tensor cores
+  size_t n_done = 0;
+};
+
+}  // namespace
+
+bool tc_supported(int rows, int cols) { return rows >= 1 && cols >= 1; }
+
+int tc_create(fot_ctx* c) {
+  TcState* t = new (std::nothrow) TcState();
+  if (!t) return 1;
+  const size_t a = (size_t)((c->rows + kTM - 1) / kTM) * ((c->cols + kTN - 1) / kTN);
+  const size_t b = (size_t)((c->cols + kTM - 1) / kTM) * ((c->rows + kTN - 1) / kTN);
+  t->n_done = a > b ? a : b;
+  if (cudaMalloc((void**)&t->done, t->n_done) != cudaSuccess ||
+      cudaMalloc((void**)&t->tc_terms, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemsetAsync(t->tc_terms, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+    if (t->done) cudaFree(t->done);
+    delete t;
+    return 1;
+  }
+  if (cudaFuncSetAttribute(tc_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
+    cudaFree(t->done);
+    cudaFree(t->tc_terms);
+    delete t;
+    return 1;
+  }
+  c->tc = t;
+  return 0;
+}
+
+void tc_destroy(fot_ctx* c) {
+  TcState* t = (TcState*)c->tc;
+  if (!t) return;
+  cudaFree(t->done);
+  cudaFree(t->tc_terms);
+  delete t;
+  c->tc = nullptr;
+}
+
+int64_t tc_terms(fot_ctx* c) {
+  TcState* t = (TcState*)c->tc;
+  if (!t) return 0;
+  unsigned long long v = 0;
+  cudaMemcpyAsync(&v, t->tc_terms, sizeof(v), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return (int64_t)v;
+}
+
+template <int MODE>
+static void tc_pass(fot_ctx* c, const BandArgs& a, float* plan) {
+  TcState* t = (TcState*)c->tc;
+  band_prepare(c, a, plan);
+  const size_t np = (size_t)a.n_rows * a.n_tiles;
+  const float* p_alpha = plan;
+  const int* p_lo = reinterpret_cast<const int*>(plan + np);
+  const int* p_wl = reinterpret_cast<const int*>(plan + 2 * np);
+  dim3 grid((a.len + kTN - 1) / kTN, (a.n_rows + kTM - 1) / kTM);
+  tc_pass_kernel<MODE><<<grid, kThreads, kSmemBytes, c->stream>>>(a, p_alpha, p_lo, p_wl, t->done,
+                                                                  t->tc_terms);
+  c->launches++;
+  band_simt<MODE>(c, a, plan, t->done);   // rows whose tile the tensor kernel declined
+}
+
+// One half-step with the tensor-core banded passes.
+void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
+                  float* logsum) {
+  const float cc = (float)(1.4426950408889634 / (2.0 * eps));
+  const float scale = (float)(1.4426950408889634 / eps);
+  float* cmax = c->cmax;
+  float* plan = cmax + (size_t)c->rows * ((c->cols + 31) / 32) + (size_t)c->cols * ((c->rows + 31) / 32);
+  BandArgs p{};
+  p.x = pot_in; p.cmax = cmax; p.y = c->R; p.err = c->err; p.terms = c->terms;
+  p.x_scale = scale; p.c = cc; p.eps = (float)eps;
+  p.n_rows = c->rows; p.len = c->cols;
+  p.n_chunks = (c->cols + 31) / 32; p.n_tiles = (c->cols + kTN - 1) / kTN;
+  tc_pass<0>(c, p, plan);
+  BandArgs q{};
+  q.x = c->R; q.cmax = cmax; q.y = pot_out; q.lmarg = lmarg; q.logsum = logsum; q.err = c->err;
+  q.terms = c->terms; q.x_scale = 1.f; q.c = cc; q.eps = (float)eps;
+  q.n_rows = c->cols; q.len = c->rows;
+  q.n_chunks = (c->rows + 31) / 32; q.n_tiles = (c->rows + kTN - 1) / kTN;
+  tc_pass<1>(c, q, plan);
+}
 
 }  // namespace fot

@@ -33,9 +33,12 @@ SHAPES = [(1, 1), (1, 37), (29, 1), (8, 8), (33, 47), (64, 64), (100, 130), (257
 EPSS = [0.3, 4.0, 60.0, 3000.0]
 
 
+@pytest.mark.parametrize("prec", ["banded", "dense"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("eps", EPSS)
-def test_half_steps_match_oracle(fot_lib, shape, eps):
+def test_half_steps_match_oracle(fot_lib, shape, eps, prec):
+    """Both FP32 kernels (banded windows with the tilted GEMM or exact windowed sums, and
+    the dense exact pass) against the oracle's half-step."""
     B = fot_lib
     rng = np.random.default_rng(hash((shape, eps)) % 2**32)
     g, G = _masses(rng, shape, 0.15)
@@ -45,7 +48,7 @@ def test_half_steps_match_oracle(fot_lib, shape, eps):
         G[-1, -1] = 1.0
     n = max(shape)
     psi = f32(inputs.random_potential(*shape, scale=0.3 * n * n + 5 * eps, seed=3, zero_frac=0.1))
-    ctx = B.fot_create(*shape)
+    ctx = B.fot_create(*shape, B.FOT_FP32 if prec == "banded" else B.FOT_FP32_DENSE)
     B.fot_set_problem(ctx, to_dev(g), to_dev(G))
     f_gpu, S_gpu = B.fot_u_update(ctx, to_dev(psi), eps, with_logsum=True)
     psi_gpu, T_gpu = B.fot_v_update(ctx, f_gpu, eps, with_logsum=True)
@@ -130,9 +133,29 @@ def test_moments_kernel_matches_oracle(fot_lib, shape, eps):
     phi, Dx, Dy = (to_np(t) for t in B.fot_moments(ctx, to_dev(psi), to_dev(S), eps, dx))
     Dx_r, Dy_r = fot.moments(psi, S, eps, dx)
     phi_r = fot.integrate_trapezoid(Dx_r, Dy_r, dx)
-    for got, ref in ((Dx, Dx_r), (Dy, Dy_r), (phi, phi_r)):
-        assert np.abs(got - ref).max() <= 2e-6 * max(np.abs(ref).max(), 1e-3)
+    # FP32 log-domain values of magnitude |v| carry absolute errors of 2^-24 |v|, which become
+    # relative errors of the exponential weights: bound from the largest log value involved
+    # (S and psi/eps, in log2 units), times the largest coordinate.
+    lmax = (np.abs(S).max() + np.abs(psi[np.isfinite(psi)]).max() / eps) / np.log(2)
+    cmax = max(shape) / 2 / (min(shape) * dx)
+    tol = 4 * 2.0 ** -24 * lmax * cmax + 1e-6 * max(np.abs(Dx_r).max(), 1e-3)
+    assert np.abs(Dx - Dx_r).max() <= tol and np.abs(Dy - Dy_r).max() <= tol
+    assert np.abs(phi - phi_r).max() <= tol * max(shape) * dx
     ctx.close()
+
+
+def test_work_counter(fot_lib):
+    B = fot_lib
+    ctx = B.fot_create(40, 56, B.FOT_FP32_DENSE)
+    g = torch.rand(40, 56, device="cuda") + 0.1
+    B.fot_solve(ctx, g, g, [2.0], 3)
+    assert B.fot_work_count(ctx) == 3 * 2 * (40 * 56 * 56 + 56 * 40 * 40)
+    ctx2 = B.fot_create(40, 56, B.FOT_FP32)
+    B.fot_solve(ctx2, g, g, [2.0], 3)
+    t = B.fot_work_count(ctx2)
+    assert 0 < t <= 3 * 2 * (40 * 56 * 56 + 56 * 40 * 40) * 2
+    ctx.close()
+    ctx2.close()
 
 
 def test_gaussian_closed_form_phase(fot_lib):
@@ -319,3 +342,81 @@ def test_host_buffer_entry_point(fot_lib, c1_ref):
     assert normwise(phi.double().numpy(), r["phi"]) <= 2e-6
     assert B.fot_launch_count(ctx) > 4 * w.iters
     ctx.close()
+
+
+# ---------------------------------------------------------------------------------------
+# mixed precision: the banded GEMM on tcgen05 tensor cores with split-BF16 operands
+# ---------------------------------------------------------------------------------------
+# Bound: every product is hi*hi + hi*lo + lo*hi of two-part BF16 operands, missing lo*lo and
+# the rounding of the lo parts, i.e. < 2^-16 relative; all terms are positive, so each window
+# sum is within 2^-16 relative and each pass adds < 2^-16 / ln 2 to a log2 output.  Two passes
+# per half-step: |df| <= eps * ln 2 * 2 * 2^-16 / ln 2 = 2^-15 eps, plus FP32 rounding.
+def mixed_atol(eps):
+    return 2.0 ** -15 * eps
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (100, 130), (257, 200), (300, 300)])
+@pytest.mark.parametrize("eps", [60.0, 3000.0])
+def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
+    B = fot_lib
+    rng = np.random.default_rng(hash((shape, eps, "mixed")) % 2**32)
+    g, G = _masses(rng, shape, 0.15)
+    n = max(shape)
+    psi = f32(inputs.random_potential(*shape, scale=0.3 * n * n + 5 * eps, seed=3, zero_frac=0.1))
+    ctx = B.fot_create(*shape, B.FOT_MIXED)
+    B.fot_set_problem(ctx, to_dev(g), to_dev(G))
+    f_gpu, S_gpu = B.fot_u_update(ctx, to_dev(psi), eps, with_logsum=True)
+    B.fot_sync(ctx)
+    _, tensor_terms = B.fot_work_count(ctx, tensor=True)
+    la = fot.log0(fot.marginal(g))
+    f_ref, S_ref = fot.u_update(psi, la, eps)
+    f_np = to_np(f_gpu)
+    fin = np.isfinite(f_ref)
+    assert np.array_equal(np.isneginf(f_np), np.isneginf(f_ref))
+    err = np.abs(f_np[fin] - f_ref[fin]).max()
+    assert err <= POT_RTOL * np.abs(f_ref[fin]).max() + mixed_atol(eps), (err, mixed_atol(eps))
+    if eps >= 3000.0:
+        assert tensor_terms > 0          # these tiles satisfy the tilt bounds: tensor cores used
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_mixed_full_size_half_step_sampled(fot_lib, n):
+    B = fot_lib
+    w = inputs.config3(n)
+    eps = float(w.eps[0])
+    g, G = f32(w.g), f32(w.G)
+    psi = f32(inputs.random_potential(n, n, scale=0.3 * n * n, seed=7))
+    psi[f32(w.G) == 0] = -np.inf
+    ctx = B.fot_create(n, n, B.FOT_MIXED)
+    B.fot_set_problem(ctx, to_dev(g), to_dev(G))
+    f_gpu = to_np(B.fot_u_update(ctx, to_dev(psi), eps))
+    _, tensor_terms = B.fot_work_count(ctx, tensor=True)
+    assert tensor_terms > 0
+    rng = np.random.default_rng(n + 1)
+    samples = [(int(rng.integers(n)), int(k)) for k in rng.integers(0, n, size=16) for _ in range(4)]
+    ref = _sampled_S(psi, eps, samples)
+    la = fot.log0(fot.marginal(g))
+    f_scale = np.abs(f_gpu[np.isfinite(f_gpu)]).max()
+    for (j, k), S in ref.items():
+        f_ref = eps * (la[j, k] - S)
+        if np.isfinite(f_ref):
+            assert abs(f_gpu[j, k] - f_ref) <= POT_RTOL * f_scale + mixed_atol(eps)
+        else:
+            assert f_gpu[j, k] == -np.inf
+    ctx.close()
+
+
+def test_mixed_solve_marginal_matches_fp32(fot_lib):
+    """Benchmark workload at 1024^2, 200 iterations: the mixed iterate's marginal L1 equals
+    the FP32 iterate's to within 1e-4 (the marginal-error requirement of the mixed form)."""
+    B = fot_lib
+    w = inputs.config3(1024)
+    g, G = to_dev(f32(w.g)), to_dev(f32(w.G))
+    out = {}
+    for name, prec in (("fp32", B.FOT_FP32), ("mixed", B.FOT_MIXED)):
+        ctx = B.fot_create(1024, 1024, prec)
+        B.fot_solve(ctx, g, G, w.eps, w.iters)
+        out[name] = B.fot_marginal_error(ctx)[0]
+        ctx.close()
+    assert abs(out["mixed"] - out["fp32"]) <= 1e-4, out
