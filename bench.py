@@ -41,6 +41,9 @@ def _args():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="single", choices=["single", "batched"],
+                   help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
+                        "against looping single solves of the same problems")
     return p.parse_args()
 
 
@@ -324,10 +327,76 @@ def run_gpu(a):
     return 0
 
 
+def run_batched(a):
+    """64 problems, n_i in {128,...,512}, eps 32 -> 1 px^2 over 200 iterations: one batched
+    solve (multi-problem launches replayed as a CUDA graph) vs a loop of single solves."""
+    import torch
+    from paper_2512_19072_gb300 import binding as B
+    from paper_2512_19072_gb300 import inputs
+    ws = _workload_batched = inputs.config5(iters=a.iters)
+    prec = {"fp32": B.FOT_FP32, "fp32_dense": B.FOT_FP32, "mixed": B.FOT_MIXED}[a.precision]
+    gs = [torch.from_numpy(w.g.astype(np.float32)).cuda() for w in ws]
+    Gs = [torch.from_numpy(w.G.astype(np.float32)).cuda() for w in ws]
+    eps = np.stack([w.eps for w in ws])
+    pix_iters = sum(w.g.size for w in ws) * a.iters
+    batch = B.fot_batch_create([w.g.shape for w in ws], prec)
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        B.fot_batch_solve(batch, gs, Gs, eps, a.iters)
+    torch.cuda.synchronize()
+    clocks = _Clocks(torch.cuda.current_device())
+    t_b = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.fot_batch_solve(batch, gs, Gs, eps, a.iters)
+        e1.record(stream)
+        t_b.append((e0, e1))
+    torch.cuda.synchronize()
+    ms_b = statistics.median(e0.elapsed_time(e1) for e0, e1 in t_b)
+    kernels, tensor = B.fot_batch_info(batch)
+    ctxs = [B.fot_create(*w.g.shape, prec) for w in ws]
+    def loop():
+        for c, g, G, w in zip(ctxs, gs, Gs, ws):
+            B.fot_solve(c, g, G, w.eps, a.iters)
+    loop()
+    torch.cuda.synchronize()
+    t_l = []
+    for _ in range(max(1, a.steps // 2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loop()
+        e1.record(stream)
+        t_l.append((e0, e1))
+    torch.cuda.synchronize()
+    ms_l = statistics.median(e0.elapsed_time(e1) for e0, e1 in t_l)
+    clk = clocks.stop()
+    l1 = [B.fot_marginal_error(B.fot_batch_context(batch, q))[0] for q in range(len(ws))]
+    line = {"metric": "FOT Mpixel*iter/s, 64-problem uneven batch (config 5)",
+            "value": pix_iters / (ms_b * 1e-3) / 1e6, "unit": "Mpixel*iter/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if tensor else "f32",
+            "data": "synthetic (seeded Gaussian / two-Gaussian beams -> 2-6 shape targets)",
+            "config": {"workload": "c5_64_problems_128_to_512", "iters_per_solve": a.iters,
+                       "eps": "geometric 32 -> 1 px^2", "precision": a.precision,
+                       "sizes": sorted(int(w.g.shape[0]) for w in ws),
+                       "step": "fot_batch_solve (one CUDA graph launch)"},
+            "loop_of_single_solves": {"value": pix_iters / (ms_l * 1e-3) / 1e6, "ms": ms_l},
+            "speedup_vs_loop": ms_l / ms_b, "kernels_per_graph": kernels, "tensor_path": tensor,
+            "marginal_l1_max": max(l1), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    batch.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return run_batched(a)
     return run_gpu(a)
 
 

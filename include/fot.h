@@ -62,8 +62,10 @@ typedef enum {
                             log-sum-exp */
   FOT_MIXED = 1,         /* the banded GEMM on tcgen05 tensor cores (split-BF16 operands,
                             FP32 accumulation in TMEM) with FP32 log-domain potentials */
-  FOT_FP32_DENSE = 2     /* FP32 on the CUDA cores, every output scans every term with its
+  FOT_FP32_DENSE = 2,    /* FP32 on the CUDA cores, every output scans every term with its
                             own exact maximum (one exponential per term): the plain form */
+  FOT_AUTO = 3           /* batches only: time FOT_FP32 and FOT_MIXED on the batch when its
+                            graph is built and keep the faster */
 } fot_precision;
 
 typedef enum { FOT_EPS_PX2 = 0, FOT_EPS_PAPER = 1 } fot_eps_units;
@@ -167,6 +169,42 @@ fot_status fot_v_update(fot_ctx* ctx, const float* f_in, double eps, float* psi_
 #define FOT_NOALLOC_MAX_PIXELS (1024 * 1024)
 fot_status fot_u_update_noalloc(const float* psi_in, const float* log_a, int rows, int cols,
                                 double eps, float* f_out, float* logsum_out, void* cuda_stream);
+
+/* Batched solve: `count` (<= 64) independent problems of their own grid sizes, solved
+ * together (Algorithm 1 for each).  Every axis pass of every problem runs in the same
+ * multi-problem launches, and the whole solve (setup and all iterations) is captured once
+ * into a CUDA graph that each fot_batch_solve replays with one graph launch; the graph is
+ * rebuilt when the input pointers, the schedule or the iteration count change.  rows, cols:
+ * host arrays of count sizes; precision FOT_FP32, FOT_MIXED or FOT_AUTO.  The batch owns one
+ * fot_ctx per problem (fot_batch_context), through which the results are read with
+ * fot_potentials / fot_phase / fot_marginal_error. */
+typedef struct fot_batch fot_batch;
+fot_status fot_batch_create(fot_batch** out, int count, const int* rows, const int* cols,
+                            int precision, int device, void* cuda_stream);
+void fot_batch_destroy(fot_batch* batch);
+fot_ctx* fot_batch_context(fot_batch* batch, int index);
+
+/* g, G: host arrays of `count` device pointers (problem q is rows[q] x cols[q]); eps: host
+ * array [count][n_eps] (n_eps == 1 fixed, == iters a per-iteration schedule, per problem);
+ * dx as in fot_solve.  Asynchronous; errors per problem through its context. */
+fot_status fot_batch_solve(fot_batch* batch, const float* const* g, const float* const* G,
+                           double dx, const double* eps, int n_eps, int eps_units, int iters);
+
+/* Kernels per graph launch and whether the tensor-core form was chosen (FOT_AUTO). */
+fot_status fot_batch_info(fot_batch* batch, int64_t* kernels_per_solve, int* tensor_path);
+
+/* Reverse-mode gradient of a scalar loss L of the phase and/or the final potentials of the
+ * last fot_solve (Algorithm 1 from its standard start, any eps schedule) with respect to the
+ * amplitudes g and G, through every unrolled iteration (Eqs. 7-8), the moments (Eqs. 9-10),
+ * the trapezoid integration and the normalisation a = g^2/sum g^2, b = G^2/sum G^2.
+ * g, G: the device amplitudes of that solve; dL_dphi, dL_df, dL_dpsi: device rows x cols
+ * seeds (each may be NULL = 0); dL_dg, dL_dG: device outputs (0 where the amplitude is 0).
+ * The forward is recomputed from potentials checkpointed every checkpoint_every iterations,
+ * holding one segment (4 images per iteration) at a time; temporary device memory is
+ * allocated for the call.  Invalidated by fot_set_potentials.  Synchronising. */
+fot_status fot_backward(fot_ctx* ctx, const float* g, const float* G, const float* dL_dphi,
+                        const float* dL_df, const float* dL_dpsi, int checkpoint_every,
+                        float* dL_dg, float* dL_dG);
 
 /* Exact c-transform, the eps -> 0 limit of a half-step (the log a term vanishes):
  *   out_jk = min_LM [ ((j-L)^2 + (k-M)^2)/2 - pot_LM ],

@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-FOT_FP32, FOT_MIXED, FOT_FP32_DENSE = 0, 1, 2
+FOT_FP32, FOT_MIXED, FOT_FP32_DENSE, FOT_AUTO = 0, 1, 2, 3
 FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
 STATUS = {0: "FOT_OK", 1: "FOT_EINVAL", 2: "FOT_ENOMEM", 3: "FOT_ECUDA", 4: "FOT_ENONFINITE",
           5: "FOT_ETIMEOUT", 6: "FOT_EMASS", 7: "FOT_EUNSUPPORTED", 8: "FOT_ESTATE"}
@@ -55,6 +55,12 @@ _SIGS = {
     "fot_loop_time": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
     "fot_work_count": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "fot_status_string": (ctypes.c_char_p, [_I]),
+    "fot_backward": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
+    "fot_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _I, _P]),
+    "fot_batch_destroy": (None, [_P]),
+    "fot_batch_context": (_P, [_P, _I]),
+    "fot_batch_solve": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _DP, _I, _I, _I]),
+    "fot_batch_info": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -254,6 +260,116 @@ def fot_work_count(ctx, tensor=False):
     n, t = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.fot_work_count(ctx._h, ctypes.byref(n), ctypes.byref(t)), "fot_work_count")
     return (n.value, t.value) if tensor else n.value
+
+
+class _View(Context):
+    """A context owned by a batch (not destroyed on its own)."""
+
+    def __init__(self, handle, rows, cols, device):
+        self._h = ctypes.c_void_p(handle)
+        self.rows, self.cols, self.device = rows, cols, device
+
+    def close(self):
+        self._h = None
+
+    __del__ = close
+
+
+class Batch:
+    """fot_batch: many problems of their own sizes solved together (one graph launch)."""
+
+    def __init__(self, sizes, precision=FOT_FP32, device=None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.sizes = [tuple(s) for s in sizes]
+        self.device = device
+        n = len(self.sizes)
+        rows = (_I * n)(*[s[0] for s in self.sizes])
+        cols = (_I * n)(*[s[1] for s in self.sizes])
+        h = _P()
+        with torch.cuda.device(device):
+            _check(_lib.fot_batch_create(ctypes.byref(h), n, rows, cols, precision, device, _stream()),
+                   "fot_batch_create")
+        self._h = h
+        self.contexts = [_View(_lib.fot_batch_context(h, q), *self.sizes[q], device) for q in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for c in self.contexts:
+                c.close()
+            _lib.fot_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def fot_batch_create(sizes, precision=FOT_FP32, device=None):
+    return Batch(sizes, precision, device)
+
+
+def fot_batch_destroy(batch):
+    batch.close()
+
+
+def fot_batch_context(batch, index):
+    return batch.contexts[index]
+
+
+def fot_batch_solve(batch, gs, Gs, eps, iters, dx=0.0, eps_units=FOT_EPS_PX2):
+    """gs, Gs: lists of CUDA tensors; eps: array [count] or [count, n_eps] of px^2 values."""
+    n = len(gs)
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(n, -1))
+    ep = e.ctypes.data_as(_DP)
+    gp = (_P * n)(*[_ptr(t) for t in gs])
+    Gp = (_P * n)(*[_ptr(t) for t in Gs])
+    _check(_lib.fot_batch_solve(batch._h, gp, Gp, float(dx), ep, e.shape[1], eps_units, int(iters)),
+           "fot_batch_solve")
+    batch._keep = (e, gs, Gs)
+
+
+def fot_batch_info(batch):
+    k, t = ctypes.c_int64(), _I()
+    _check(_lib.fot_batch_info(batch._h, ctypes.byref(k), ctypes.byref(t)), "fot_batch_info")
+    return k.value, bool(t.value)
+
+
+def fot_backward(ctx, g, G, dL_dphi=None, dL_df=None, dL_dpsi=None, checkpoint_every=10):
+    dg, dG = torch.empty_like(g), torch.empty_like(G)
+    ctx._sync_stream()
+    _check(_lib.fot_backward(ctx._h, _ptr(g), _ptr(G), _ptr(dL_dphi), _ptr(dL_df), _ptr(dL_dpsi),
+                             int(checkpoint_every), _ptr(dg), _ptr(dG)), "fot_backward")
+    return dg, dG
+
+
+class FOTPhase(torch.autograd.Function):
+    """phi (and the final potentials f, psi) of Algorithm 1 as a differentiable function of the
+    amplitudes g, G: forward = fot_solve + fot_phase, backward = fot_backward (hand-written
+    adjoint kernels through the unrolled iterations, checkpointed)."""
+
+    @staticmethod
+    def forward(fctx, g, G, eps, iters, dx, precision, checkpoint_every):
+        g = g.detach().contiguous().float()
+        G = G.detach().contiguous().float()
+        ctx = fot_create(g.shape[0], g.shape[1], precision, g.device.index)
+        fot_solve(ctx, g, G, eps, iters, dx)
+        phi, _, _ = fot_phase(ctx)
+        f, psi = fot_potentials(ctx)
+        fctx.fot = ctx
+        fctx.k = checkpoint_every
+        fctx.save_for_backward(g, G)
+        return phi, f, psi
+
+    @staticmethod
+    def backward(fctx, dphi, df, dpsi):
+        g, G = fctx.saved_tensors
+        c = lambda t: None if t is None else t.contiguous().float()
+        dg, dG = fot_backward(fctx.fot, g, G, c(dphi), c(df), c(dpsi), fctx.k)
+        fctx.fot.close()
+        return dg, dG, None, None, None, None, None
+
+
+def fot_phase_fn(g, G, eps, iters, dx=0.0, precision=FOT_FP32, checkpoint_every=10):
+    return FOTPhase.apply(g, G, eps, iters, dx, precision, checkpoint_every)
 
 
 def exported_symbols():

@@ -221,6 +221,7 @@ static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int u
     // Eq. 8: psi = eps (log b - log(Lambda u Lambda))
     half_step(c, c->f, c->lb, e, c->psi, nullptr);
     c->eps_last = e;
+    c->sched.push_back(e);
   }
   cudaEventRecord(c->ev_loop1, c->stream);
   c->loop_passes = c->launches - l0;
@@ -245,6 +246,7 @@ fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, cons
   set_problem_simt(c, g, G, c->psi, psi0);
   c->have_problem = true;
   c->have_solution = false;
+  c->sched.clear();
   return run_iterations(c, eps, n_eps, eps_units, iters);
 }
 
@@ -276,6 +278,7 @@ fot_status fot_potentials(fot_ctx* c, float* f_out, float* psi_out) {
 fot_status fot_set_potentials(fot_ctx* c, const float* f, const float* psi) {
   if (!c || bad_ptr(psi)) return FOT_EINVAL;
   if (!c->have_problem) return FOT_ESTATE;
+  c->sched.clear();   // the backward recomputes from the standard start: no longer valid
   FOT_CUDA(cudaSetDevice(c->device));
   const size_t bytes = (size_t)c->rows * c->cols * sizeof(float);
   if (f) FOT_CUDA(cudaMemcpyAsync(c->f, f, bytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -377,3 +380,11 @@ fot_status fot_solve_phase_host(fot_ctx* c, const float* g_host, const float* G_
 }
 
 }  // extern "C"
+
+namespace fot {
+// the configured half-step (FP32 banded, dense or tensor-core) for the adjoint
+void half_step_dispatch(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
+                        float* logsum) {
+  half_step(c, pot_in, lmarg, eps, pot_out, logsum);
+}
+}  // namespace fot

@@ -12,7 +12,7 @@
 //    e_r(m, o) = x_r[m] - (o - m)^2 c, and its argmax.  e_r(m, o) - e_r(m', o) =
 //    x_m - x_m' - (m^2 - m'^2) c + 2 o (m - m') c grows with o when m > m', so the leftmost
 //    argmax is non-decreasing in o for any input: a divide-and-conquer monotone search finds
-//    all centres' maxima with O(len log n_tiles) evaluations per row.
+//    the maxima of a group of 16 centres with O(len log 16) evaluations.
 // 2. A provable window: every o in the tile has max_m e_r(m, o) >= LB_r, with LB_r the
 //    value of the centre's argmax term at the worse tile end.  A 32-wide chunk of m whose
 //    upper bound (chunk maximum of x, nearest distance) over the whole tile is below
@@ -38,7 +38,6 @@ namespace fot {
 
 constexpr int kBT = 16;          // outputs per tile
 constexpr int kBR = 8;           // rows per lane (16 per warp)
-constexpr int kMaxTiles = 4096 / kBT;
 constexpr int kBW = 8;           // warps per CTA
 constexpr int kCW = 32;          // chunk width of the chunk maxima
 constexpr float kCut = 40.f;     // window cut-off, log2 units
@@ -74,37 +73,51 @@ __device__ __forceinline__ int chunk_dist(int j, int a, int b, int len) {
 }
 
 // chunk maxima: cmax[r][j] = scale * max_{m in chunk j} x[r][m]; one warp per row
-__global__ void chunk_max_kernel(const float* __restrict__ x, float scale, int n_rows, int len,
-                                 int n_chunks, float* __restrict__ cmax, const int* err) {
-  if (error_latched(err)) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n_rows) return;
-  const float* xr = x + (size_t)warp * len;
-  for (int j = 0; j < n_chunks; ++j) {
+template <int MAXP>
+__global__ void chunk_max_kernel(const __grid_constant__ BandTable<MAXP> t) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= t.rows) return;
+  const BandArgs& a = t.p[find_prob<MAXP, 0>(t, gw)];
+  if (error_latched(a.err)) return;
+  const int row = gw - a.row_base;
+  const float* xr = a.x + (size_t)row * a.len;
+  for (int j = 0; j < a.n_chunks; ++j) {
     const int m = j * kCW + lane;
-    const float v = warp_max(m < len ? xr[m] : -INFINITY);
-    if (lane == 0) cmax[(size_t)warp * n_chunks + j] = v * scale;
+    const float v = warp_max(m < a.len ? xr[m] : -INFINITY);
+    if (lane == 0) a.cmax[(size_t)row * a.n_chunks + j] = v * a.x_scale;
   }
 }
 
 // Per (row, tile) plan: exact centre offset alpha, window start lo and length wl.  One warp
-// per row: the monotone search evaluates lane-parallel scans of contiguous ranges of m; the
-// windows are then found with one lane per tile.
-__global__ void __launch_bounds__(256) band_plan_kernel(BandArgs a, float* __restrict__ p_alpha,
-                                                        int* __restrict__ p_lo, int* __restrict__ p_wl) {
-  __shared__ float s_al[8][kMaxTiles];
-  __shared__ int s_arg[8][kMaxTiles];
-  __shared__ int4 s_stack[8][40];
-  if (error_latched(a.err)) return;
+// per (row, group of 16 tiles): the monotone search runs over the group's centres with
+// lane-parallel scans of contiguous ranges of m (the group's first scan covers the whole
+// row); the windows are then found with one lane per tile.
+constexpr int kPlanGroup = 16;
+
+template <int MAXP>
+__global__ void __launch_bounds__(256) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+  __shared__ float s_al[8][kPlanGroup];
+  __shared__ int s_arg[8][kPlanGroup];
+  __shared__ int4 s_stack[8][16];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * 8 + w;
-  if (row >= a.n_rows) return;                            // warp-uniform
-  const float c = a.c, sc = a.x_scale;
+  const int gw = blockIdx.x * 8 + w;
+  if (gw >= tab.plans) return;                            // warp-uniform
+  const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, gw)];
+  if (error_latched(a.err)) return;
   const int T = a.n_tiles, len = a.len;
+  const int groups = (T + kPlanGroup - 1) / kPlanGroup;
+  const int lw = gw - a.plan_base;
+  const size_t np = (size_t)a.n_rows * T;
+  float* p_alpha = a.plan;
+  int* p_lo = reinterpret_cast<int*>(a.plan + np);
+  int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
+  const int row = lw / groups, t0 = (lw % groups) * kPlanGroup;
+  const int t1 = min(t0 + kPlanGroup, T) - 1;
+  const float c = a.c, sc = a.x_scale;
   const float* xr = a.x + (size_t)row * len;
-  // 1. monotone divide and conquer over the tile centres (depth-first, left child first)
+  // 1. monotone divide and conquer over the group's centres (depth-first, left child first)
   int sp = 1;
-  if (lane == 0) s_stack[w][0] = make_int4(0, T - 1, 0, len - 1);
+  if (lane == 0) s_stack[w][0] = make_int4(t0, t1, 0, len - 1);
   bool row_empty = false;
   __syncwarp();
   while (sp > 0) {
@@ -119,6 +132,7 @@ __global__ void __launch_bounds__(256) band_plan_kernel(BandArgs a, float* __res
       // pass 1 only when the restricted range held no finite term (rounding can break the
       // monotone order by an ulp): then scan the whole row
       const int mlo = pass == 0 ? e.z : 0, mhi = pass == 0 ? e.w : len - 1;
+#pragma unroll 4
       for (int m = mlo + lane; m <= mhi; m += 32) {
         const float d = (float)(kc - m);
         const float v = fmaf(-d * d, c, xr[m] * sc);
@@ -136,8 +150,8 @@ __global__ void __launch_bounds__(256) band_plan_kernel(BandArgs a, float* __res
     }
     __syncwarp();
     if (lane == 0) {
-      s_al[w][mid] = best;
-      s_arg[w][mid] = arg;
+      s_al[w][mid - t0] = best;
+      s_arg[w][mid - t0] = arg;
       s_stack[w][sp] = make_int4(mid + 1, e.y, arg, e.w);
       s_stack[w][sp + 1] = make_int4(e.x, mid - 1, e.z, arg);
     }
@@ -146,51 +160,53 @@ __global__ void __launch_bounds__(256) band_plan_kernel(BandArgs a, float* __res
   }
   // 2. windows, one lane per tile
   const float* cm = a.cmax + (size_t)row * a.n_chunks;
-  for (int t = lane; t < T; t += 32) {
-    const size_t pi = (size_t)row * T + t;
-    const float al = s_al[w][t];
-    if (al == -INFINITY) {
-      p_alpha[pi] = -INFINITY;
-      p_lo[pi] = 0;
-      p_wl[pi] = 0;
-      continue;
-    }
-    const int k0 = t * kBT, kc = k0 + kBT / 2, k1 = min(k0 + kBT, len) - 1;
-    const float dM = (float)(s_arg[w][t] - kc);
-    const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
-    const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
-    int jlo = a.n_chunks, jhi = -1;
-    for (int j = 0; j < a.n_chunks; ++j) {
-      const float d = (float)chunk_dist(j, k0, k1, len);
-      if (fmaf(-d * d, c, cm[j]) >= lb - kCut) {
-        jlo = min(jlo, j);
-        jhi = j;
-      }
-    }
-    p_alpha[pi] = al;
-    p_lo[pi] = jlo * kCW;
-    p_wl[pi] = min((jhi + 1) * kCW, len) - jlo * kCW;
+  const int t = t0 + lane;
+  if (lane >= kPlanGroup || t > t1) return;
+  const size_t pi = (size_t)row * T + t;
+  const float al = s_al[w][lane];
+  if (al == -INFINITY) {
+    p_alpha[pi] = -INFINITY;
+    p_lo[pi] = 0;
+    p_wl[pi] = 0;
+    return;
   }
+  const int k0 = t * kBT, kc = k0 + kBT / 2, k1 = min(k0 + kBT, len) - 1;
+  const float dM = (float)(s_arg[w][lane] - kc);
+  const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
+  const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
+  int jlo = a.n_chunks, jhi = -1;
+  for (int j = 0; j < a.n_chunks; ++j) {
+    const float d = (float)chunk_dist(j, k0, k1, len);
+    if (fmaf(-d * d, c, cm[j]) >= lb - kCut) {
+      jlo = min(jlo, j);
+      jhi = j;
+    }
+  }
+  p_alpha[pi] = al;
+  p_lo[pi] = jlo * kCW;
+  p_wl[pi] = min((jhi + 1) * kCW, len) - jlo * kCW;
 }
 
 // PATH 0 handles the items that take the tilted GEMM, PATH 1 the exact-window items; the two
 // variants are launched back to back and each skips the other's items (lean registers).
 constexpr int kSA = 8 * 36 + 4;   // floats per half-warp A block (8 rows x 36, +4: banks)
 
-template <int MODE, int PATH>
-__global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(BandArgs a, const float* __restrict__ p_alpha,
-                                                                const int* __restrict__ p_lo,
-                                                                const int* __restrict__ p_wl,
-                                                                const unsigned char* __restrict__ skip) {
+template <int MODE, int PATH, int MAXP>
+__global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   __shared__ __align__(16) float sA[kBW][2 * kSA];
-  if (error_latched(a.err)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int h = lane >> 4, i = lane & 15;
   const int gw = blockIdx.x * kBW + warp;
-  const int n_rg = (a.n_rows + 2 * kBR - 1) / (2 * kBR);
-  if (gw >= n_rg * a.n_tiles) return;                     // warp-uniform
-  const int tile = gw % a.n_tiles, r0 = (gw / a.n_tiles) * 2 * kBR;
-  if (skip && skip[(size_t)(r0 / 128) * a.n_tiles + tile]) return;   // done on the tensor cores
+  if (gw >= tab.items) return;                            // warp-uniform
+  const BandArgs& a = tab.p[find_prob<MAXP, 2>(tab, gw)];
+  if (error_latched(a.err)) return;
+  const int lw = gw - a.item_base;
+  const int tile = lw % a.n_tiles, r0 = (lw / a.n_tiles) * 2 * kBR;
+  if (a.skip && a.skip[(size_t)(r0 / 128) * a.n_tiles + tile]) return;   // done on the tensor cores
+  const size_t np = (size_t)a.n_rows * a.n_tiles;
+  const float* __restrict__ p_alpha = a.plan;
+  const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
+  const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
   const int rh = r0 + h * kBR;                             // this half's first row
   const int k0 = tile * kBT, kc = k0 + kBT / 2;
   const int k1 = min(k0 + kBT, a.len) - 1;
@@ -354,60 +370,86 @@ __global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(BandArgs a, cons
   }
 }
 
-static void chunk_max(fot_ctx* c, const float* x, float scale, int n_rows, int len, float* cmax) {
-  const int nch = (len + kCW - 1) / kCW;
-  const int warps_per_block = 8;
-  chunk_max_kernel<<<(n_rows + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0,
-                     c->stream>>>(x, scale, n_rows, len, nch, cmax, c->err);
-  c->launches++;
+template <int MAXP>
+void band_table_finish(BandTable<MAXP>& t) {
+  int rows = 0, plans = 0, items = 0, ctas = 0;
+  for (int q = 0; q < t.n; ++q) {
+    BandArgs& a = t.p[q];
+    a.n_chunks = (a.len + kCW - 1) / kCW;
+    a.n_tiles = (a.len + kBT - 1) / kBT;
+    a.row_base = rows;
+    a.plan_base = plans;
+    a.item_base = items;
+    a.cta_base = ctas;
+    rows += a.n_rows;
+    plans += a.n_rows * ((a.n_tiles + kPlanGroup - 1) / kPlanGroup);
+    items += ((a.n_rows + 2 * kBR - 1) / (2 * kBR)) * a.n_tiles;
+    ctas += ((a.n_rows + 127) / 128) * a.n_tiles;
+  }
+  t.rows = rows;
+  t.plans = plans;
+  t.items = items;
+  t.ctas = ctas;
 }
 
-void band_prepare(fot_ctx* c, const BandArgs& a, float* plan) {
-  chunk_max(c, a.x, a.x_scale, a.n_rows, a.len, const_cast<float*>(a.cmax));
-  const size_t np = (size_t)a.n_rows * a.n_tiles;
-  band_plan_kernel<<<(a.n_rows + 7) / 8, 256, 0, c->stream>>>(
-      a, plan, reinterpret_cast<int*>(plan + np), reinterpret_cast<int*>(plan + 2 * np));
-  c->launches++;
+template <int MAXP>
+void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
+  chunk_max_kernel<MAXP><<<(t.rows + 7) / 8, 256, 0, s>>>(t);
+  band_plan_kernel<MAXP><<<(t.plans + 7) / 8, 256, 0, s>>>(t);
 }
 
-template <int MODE>
-void band_simt(fot_ctx* c, const BandArgs& a, const float* plan, const unsigned char* skip) {
-  const size_t np = (size_t)a.n_rows * a.n_tiles;
-  const float* p_alpha = plan;
-  const int* p_lo = reinterpret_cast<const int*>(plan + np);
-  const int* p_wl = reinterpret_cast<const int*>(plan + 2 * np);
-  const int n_rg = (a.n_rows + 2 * kBR - 1) / (2 * kBR);
-  const int warps = n_rg * a.n_tiles;
-  band_pass_kernel<MODE, 0><<<(warps + kBW - 1) / kBW, kBW * 32, 0, c->stream>>>(a, p_alpha, p_lo, p_wl, skip);
-  band_pass_kernel<MODE, 1><<<(warps + kBW - 1) / kBW, kBW * 32, 0, c->stream>>>(a, p_alpha, p_lo, p_wl, skip);
-  c->launches += 2;
+template <int MODE, int MAXP>
+void band_simt(cudaStream_t s, const BandTable<MAXP>& t) {
+  band_pass_kernel<MODE, 0, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
+  band_pass_kernel<MODE, 1, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
 }
-template void band_simt<kBandLse>(fot_ctx*, const BandArgs&, const float*, const unsigned char*);
-template void band_simt<kBandPot>(fot_ctx*, const BandArgs&, const float*, const unsigned char*);
+
+template void band_table_finish<1>(BandTable<1>&);
+template void band_table_finish<kMaxBatch>(BandTable<kMaxBatch>&);
+template void band_prepare<1>(cudaStream_t, const BandTable<1>&);
+template void band_prepare<kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template void band_simt<kBandLse, 1>(cudaStream_t, const BandTable<1>&);
+template void band_simt<kBandPot, 1>(cudaStream_t, const BandTable<1>&);
+template void band_simt<kBandLse, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template void band_simt<kBandPot, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+
+// the two passes of one half-step for one context
+BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale) {
+  BandArgs a{};
+  a.x = x;
+  a.cmax = c->cmax;
+  a.plan = c->cmax + (size_t)c->rows * ((c->cols + kCW - 1) / kCW) + (size_t)c->cols * ((c->rows + kCW - 1) / kCW);
+  a.err = c->err;
+  a.terms = c->terms;
+  a.x_scale = x_scale;
+  a.c = (float)(1.4426950408889634 / (2.0 * eps));
+  a.eps = (float)eps;
+  a.n_rows = n_rows;
+  a.len = len;
+  return a;
+}
 
 // One half-step with banded passes: pot_out = eps (lmarg - log(Lambda exp(pot_in/eps) Lambda)).
 void half_step_band(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                     float* pot_out, float* logsum, float* tmp, float* cmax) {
-  float* plan = cmax + (size_t)c->rows * ((c->cols + kCW - 1) / kCW) + (size_t)c->cols * ((c->rows + kCW - 1) / kCW);
-  const float cc = (float)(1.4426950408889634 / (2.0 * eps));
-  const float scale = (float)(1.4426950408889634 / eps);
-  // pass over the contiguous axis: rows = rows of pot_in, outputs along cols
-  BandArgs p{};
-  p.x = pot_in; p.cmax = cmax; p.y = tmp; p.err = c->err; p.terms = c->terms;
-  p.x_scale = scale; p.c = cc; p.eps = (float)eps;
-  p.n_rows = c->rows; p.len = c->cols;
-  p.n_chunks = (c->cols + kCW - 1) / kCW; p.n_tiles = (c->cols + kBT - 1) / kBT;
-  band_prepare(c, p, plan);
-  band_simt<kBandLse>(c, p, plan, nullptr);
+  (void)cmax;
+  BandTable<1> t{};
+  t.n = 1;
+  // pass over the contiguous axis: rows of pot_in, outputs along cols, written [k][L]
+  t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
+  t.p[0].y = tmp;
+  band_table_finish(t);
+  band_prepare(c->stream, t);
+  band_simt<kBandLse>(c->stream, t);
   // pass over the row axis (input tmp[k][L], log2 units) with the fused potential update
-  BandArgs q{};
-  q.x = tmp; q.cmax = cmax; q.y = pot_out; q.lmarg = lmarg; q.logsum = logsum; q.err = c->err;
-  q.terms = c->terms;
-  q.x_scale = 1.f; q.c = cc; q.eps = (float)eps;
-  q.n_rows = c->cols; q.len = c->rows;
-  q.n_chunks = (c->rows + kCW - 1) / kCW; q.n_tiles = (c->rows + kBT - 1) / kBT;
-  band_prepare(c, q, plan);
-  band_simt<kBandPot>(c, q, plan, nullptr);
+  t.p[0] = band_args(c, tmp, c->cols, c->rows, eps, 1.f);
+  t.p[0].y = pot_out;
+  t.p[0].lmarg = lmarg;
+  t.p[0].logsum = logsum;
+  band_table_finish(t);
+  band_prepare(c->stream, t);
+  band_simt<kBandPot>(c->stream, t);
+  c->launches += 8;
 }
 
 }  // namespace fot

@@ -1,30 +1,73 @@
 // Banded axis pass: arguments and entry points shared by the CUDA-core kernels
-// (fot_band.cu) and the tensor-core kernel (fot_tc.cu).
+// (fot_band.cu), the tensor-core kernel (fot_tc.cu) and the batched solver (fot_batch.cu).
 #pragma once
 
 #include "fot_common.cuh"
 
 namespace fot {
 
+// One problem's pass.  plan holds alpha (float), window start and window length (int) per
+// (row, 16-output tile), n_rows * n_tiles words each, consecutive.
 struct BandArgs {
   const float* x;      // [n_rows][len] input
-  const float* cmax;   // [n_rows][n_chunks] chunk maxima of x * x_scale (log2 units)
+  float* cmax;         // [n_rows][n_chunks] chunk maxima of x * x_scale (log2 units)
+  float* plan;
   const float* lmarg;  // potential-update mode: natural log marginal, layout of y
   float* y;            // [len][n_rows] output (transposed)
   float* logsum;       // potential-update mode: optional natural-log LSE, layout of y
   int* err;
-  unsigned long long* terms;   // += (row, output, m) triples evaluated on the CUDA cores
+  unsigned long long* terms;     // += (row, output, m) triples evaluated on the CUDA cores
+  unsigned long long* tc_terms;  // += triples evaluated on the tensor cores
+  unsigned char* skip;           // per (128-row block, tile): taken by the tensor kernel
   float x_scale, c, eps;
   int n_rows, len, n_chunks, n_tiles;
+  int row_base, plan_base, item_base, cta_base;   // first global work index of each kernel
 };
 
-// chunk maxima of a.x, then the per-(row, 32-output tile) plan: alpha (float), window start
-// and window length (int), each n_rows * n_tiles words, consecutive in `plan`
-void band_prepare(fot_ctx* c, const BandArgs& a, float* plan);
+constexpr int kMaxBatch = 64;
 
-// the CUDA-core window sums for every (8-row group, tile) item; items whose 128-row block
-// and tile are marked in `skip` (index (row / 128) * n_tiles + tile) are left alone
-template <int MODE>
-void band_simt(fot_ctx* c, const BandArgs& a, const float* plan, const unsigned char* skip);
+// A launch covers every problem of the table; each kernel maps its global warp (or CTA)
+// index to a problem by the *_base prefix sums.  Passed by value (__grid_constant__).
+template <int MAXP>
+struct BandTable {
+  int n;                                 // problems
+  int rows, plans, items, ctas;          // totals of the four work kinds
+  BandArgs p[MAXP];
+};
+
+// problem owning global work index gi of kind WHICH (0 rows, 1 plan warps, 2 band items,
+// 3 tensor CTAs): binary search over the prefix sums (a single problem needs none)
+template <int MAXP, int WHICH>
+__device__ __forceinline__ int find_prob(const BandTable<MAXP>& t, int gi) {
+  if (MAXP == 1) return 0;
+  int lo = 0, hi = t.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const BandArgs& q = t.p[mid];
+    const int b = WHICH == 0 ? q.row_base : WHICH == 1 ? q.plan_base : WHICH == 2 ? q.item_base : q.cta_base;
+    if (b <= gi)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// fill n_chunks, n_tiles, the *_base prefix sums and the totals
+template <int MAXP>
+void band_table_finish(BandTable<MAXP>& t);
+
+// chunk maxima and per-(row, tile) plan of every problem
+template <int MAXP>
+void band_prepare(cudaStream_t s, const BandTable<MAXP>& t);
+
+// the CUDA-core window sums; items whose (128-row block, tile) is marked in skip are left
+// alone (MODE 0: log-sum output; MODE 1: potential update)
+template <int MODE, int MAXP>
+void band_simt(cudaStream_t s, const BandTable<MAXP>& t);
+
+// the tensor-core window sums (fot_tc.cu); marks skip for the tiles it takes
+template <int MODE, int MAXP>
+void tc_pass(cudaStream_t s, const BandTable<MAXP>& t);
 
 }  // namespace fot

@@ -5,6 +5,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fot.h"
 
 namespace fot {
@@ -60,6 +62,7 @@ struct fot_ctx {
   // CUDA events bracketing the last Sinkhorn loop (only axis passes run inside it)
   cudaEvent_t ev_loop0 = nullptr, ev_loop1 = nullptr;
   int64_t loop_passes = 0;   // axis-pass launches inside the last loop
+  std::vector<double> sched; // eps (px^2) of every iteration since the last fot_solve
   // mixed-precision (tensor-core) resources, owned by fot_tc.cu
   void* tc = nullptr;
 };

@@ -121,25 +121,29 @@ __device__ __forceinline__ void store_split8(const float* v, uint32_t hi_addr, u
                "r"(pack_bf16(l[6], l[7])) : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(BandArgs a, const float* __restrict__ p_alpha,
-                                                              const int* __restrict__ p_lo,
-                                                              const int* __restrict__ p_wl,
-                                                              unsigned char* __restrict__ done,
-                                                              unsigned long long* tc_terms) {
+template <int MODE, int MAXP>
+__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ float s_alpha[kTM];
   __shared__ int s_lo[kTM];
   __shared__ int s_wmax;
+  const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, (int)blockIdx.x)];
   if (error_latched(a.err)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int blk = blockIdx.y, tile = blockIdx.x;
+  const int lb = (int)blockIdx.x - a.cta_base;
+  const int blk = lb / a.n_tiles, tile = lb % a.n_tiles;
   const int r0 = blk * kTM;
   const int k0 = tile * kTN, kc = k0 + kTN / 2;
   const int k1 = min(k0 + kTN, a.len) - 1;
   const float c = a.c, sc = a.x_scale;
+  const size_t np = (size_t)a.n_rows * a.n_tiles;
+  const float* __restrict__ p_alpha = a.plan;
+  const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
+  const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
+  unsigned char* done = a.skip;
+  unsigned long long* tc_terms = a.tc_terms;
 
   // per-row plan and the common window length
   if (tid == 0) s_wmax = 0;
@@ -197,6 +201,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(BandArgs a, const 
   const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
 
   const int nchunk = W / kKC;
+  // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
+  // multiple of 32 and each chunk starts at a multiple of 64, so the float4 loads are
+  // aligned; positions at or beyond len read -inf (the kernel skips rows without mass).
+  const bool a_live = a_alpha != -INFINITY;
+  // the 16-byte vector load needs the row base aligned too: x + row * len is 16-byte aligned
+  // only when row * len is a multiple of 4 (window starts are multiples of 32)
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(xr) & 15u) == 0;
+  float4 xq[8];
+  auto load_x = [&](int m0) {
+    const int mb = a_lo + m0 + ah * 32;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int m = mb + 4 * q;
+      if (a_live && vec_ok && m + 3 < a.len) {
+        xq[q] = __ldg(reinterpret_cast<const float4*>(xr + m));
+      } else {
+        xq[q].x = (a_live && m < a.len) ? xr[m] : -INFINITY;
+        xq[q].y = (a_live && m + 1 < a.len) ? xr[m + 1] : -INFINITY;
+        xq[q].z = (a_live && m + 2 < a.len) ? xr[m + 2] : -INFINITY;
+        xq[q].w = (a_live && m + 3 < a.len) ? xr[m + 3] : -INFINITY;
+      }
+    }
+  };
+  load_x(0);
   int issued = 0;                           // chunks whose MMAs were issued and committed
   for (int ch = 0; ch < nchunk && ok; ++ch) {
     const int s = ch & 1;
@@ -208,20 +236,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(BandArgs a, const 
     const uint32_t st = sbase + s * kStageBytes;
     const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
     const int m0 = ch * kKC;
+    float xv[32];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      xv[4 * q] = xq[q].x;
+      xv[4 * q + 1] = xq[q].y;
+      xv[4 * q + 2] = xq[q].z;
+      xv[4 * q + 3] = xq[q].w;
+    }
+    if (ch + 1 < nchunk) load_x(m0 + kKC);
     // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
+    const float dbase = (float)(kc - (a_lo + m0 + ah * 32));
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
       float v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int mp = m0 + ah * 32 + g * 8 + i;         // window position
-        const int m = a_lo + mp;
-        float e = 0.f;
-        if (a_alpha != -INFINITY && m < a.len) {
-          const float d = (float)(kc - m);
-          e = ex2(fmaf(-d * d, c, xr[m] * sc) - a_alpha);
-        }
-        v[i] = e;
+        const float d = dbase - (float)(g * 8 + i);
+        v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - (a_live ? a_alpha : 0.f));   // -inf -> 0
       }
       const int kg = ah * 4 + g;                          // core-matrix column in the stage
       const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
@@ -346,8 +378,11 @@ int tc_create(fot_ctx* c) {
     delete t;
     return 1;
   }
-  if (cudaFuncSetAttribute(tc_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(tc_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
+  // dynamic shared memory above 48 KB, for every instance (before any stream capture)
+  if (cudaFuncSetAttribute(tc_pass_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_pass_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_pass_kernel<0, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(tc_pass_kernel<1, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
     cudaFree(t->done);
     cudaFree(t->tc_terms);
     delete t;
@@ -375,40 +410,46 @@ int64_t tc_terms(fot_ctx* c) {
   return (int64_t)v;
 }
 
-template <int MODE>
-static void tc_pass(fot_ctx* c, const BandArgs& a, float* plan) {
-  TcState* t = (TcState*)c->tc;
-  band_prepare(c, a, plan);
-  const size_t np = (size_t)a.n_rows * a.n_tiles;
-  const float* p_alpha = plan;
-  const int* p_lo = reinterpret_cast<const int*>(plan + np);
-  const int* p_wl = reinterpret_cast<const int*>(plan + 2 * np);
-  dim3 grid((a.len + kTN - 1) / kTN, (a.n_rows + kTM - 1) / kTM);
-  tc_pass_kernel<MODE><<<grid, kThreads, kSmemBytes, c->stream>>>(a, p_alpha, p_lo, p_wl, t->done,
-                                                                  t->tc_terms);
-  c->launches++;
-  band_simt<MODE>(c, a, plan, t->done);   // rows whose tile the tensor kernel declined
+template <int MODE, int MAXP>
+void tc_pass(cudaStream_t s, const BandTable<MAXP>& t) {
+  tc_pass_kernel<MODE, MAXP><<<t.ctas, kThreads, kSmemBytes, s>>>(t);
 }
 
-// One half-step with the tensor-core banded passes.
+unsigned char* tc_done(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->done : nullptr; }
+unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
+template void tc_pass<0, 1>(cudaStream_t, const BandTable<1>&);
+template void tc_pass<1, 1>(cudaStream_t, const BandTable<1>&);
+template void tc_pass<0, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template void tc_pass<1, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+
+BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
+
+// One half-step with the tensor-core banded passes (CUDA-core kernels take the tiles the
+// tensor kernel declines).
 void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
                   float* logsum) {
-  const float cc = (float)(1.4426950408889634 / (2.0 * eps));
-  const float scale = (float)(1.4426950408889634 / eps);
-  float* cmax = c->cmax;
-  float* plan = cmax + (size_t)c->rows * ((c->cols + 31) / 32) + (size_t)c->cols * ((c->rows + 31) / 32);
-  BandArgs p{};
-  p.x = pot_in; p.cmax = cmax; p.y = c->R; p.err = c->err; p.terms = c->terms;
-  p.x_scale = scale; p.c = cc; p.eps = (float)eps;
-  p.n_rows = c->rows; p.len = c->cols;
-  p.n_chunks = (c->cols + 31) / 32; p.n_tiles = (c->cols + kTN - 1) / kTN;
-  tc_pass<0>(c, p, plan);
-  BandArgs q{};
-  q.x = c->R; q.cmax = cmax; q.y = pot_out; q.lmarg = lmarg; q.logsum = logsum; q.err = c->err;
-  q.terms = c->terms; q.x_scale = 1.f; q.c = cc; q.eps = (float)eps;
-  q.n_rows = c->cols; q.len = c->rows;
-  q.n_chunks = (c->rows + 31) / 32; q.n_tiles = (c->rows + kTN - 1) / kTN;
-  tc_pass<1>(c, q, plan);
+  TcState* ts = (TcState*)c->tc;
+  BandTable<1> t{};
+  t.n = 1;
+  t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
+  t.p[0].y = c->R;
+  t.p[0].skip = ts->done;
+  t.p[0].tc_terms = ts->tc_terms;
+  band_table_finish(t);
+  band_prepare(c->stream, t);
+  tc_pass<0>(c->stream, t);
+  band_simt<0>(c->stream, t);
+  t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
+  t.p[0].y = pot_out;
+  t.p[0].lmarg = lmarg;
+  t.p[0].logsum = logsum;
+  t.p[0].skip = ts->done;
+  t.p[0].tc_terms = ts->tc_terms;
+  band_table_finish(t);
+  band_prepare(c->stream, t);
+  tc_pass<1>(c->stream, t);
+  band_simt<1>(c->stream, t);
+  c->launches += 10;
 }
 
 }  // namespace fot

@@ -251,3 +251,35 @@ def test_marginal_l1_matches_dense_plan():
     D = (np.where(r["a"] > 0, r["f"] * r["a"], 0).sum() + np.where(r["b"] > 0, r["psi"] * r["b"], 0).sum()
          - eps * Gam.sum() + eps)
     assert abs(fot.dual_objective(r["f"], r["psi"], r["a"], r["b"], eps) - D) < 1e-12
+
+
+# P12: the dense autograd gradient of the phase loss (an independent dense implementation)
+# against central finite differences, and its phase against the separable oracle
+def test_p12_adjoint_oracle_vs_finite_differences():
+    from oracle import adjoint
+    rng = np.random.default_rng(12)
+    n_r, n_c = 7, 8
+    g = rng.uniform(0.3, 1.0, size=(n_r, n_c))
+    G = rng.uniform(0.3, 1.0, size=(n_r, n_c))
+    eps, iters, dx = 1.5, 6, 1 / math.sqrt(8)
+    w = rng.uniform(0, 1, size=(n_r, n_c))
+    phi_t = rng.normal(0, 0.1, size=(n_r, n_c))
+    # the dense chain reproduces the separable oracle's phase
+    import torch as _t
+    _, phi_dense = adjoint.phase_loss(_t.tensor(g), _t.tensor(G), eps, iters, _t.tensor(w), _t.tensor(phi_t), dx)
+    r = fot.fot_iterate(g, G, eps, iters)
+    phi_sep, _, _ = fot.phase(r["psi"], r["S_last"], eps, dx)
+    assert np.allclose(phi_dense.detach().numpy(), phi_sep, atol=1e-12)
+    L, dg, dG = adjoint.gradients(g, G, eps, iters, w, phi_t, dx)
+    h = 1e-3
+    for (arr, grad) in ((g, dg), (G, dG)):
+        for idx in [(0, 0), (3, 4), (6, 7), (2, 5)]:
+            p = arr.copy(); p[idx] += h
+            m = arr.copy(); m[idx] -= h
+            if arr is g:
+                fd = (adjoint.loss_value(p, G, eps, iters, w, phi_t, dx)
+                      - adjoint.loss_value(m, G, eps, iters, w, phi_t, dx)) / (2 * h)
+            else:
+                fd = (adjoint.loss_value(g, p, eps, iters, w, phi_t, dx)
+                      - adjoint.loss_value(g, m, eps, iters, w, phi_t, dx)) / (2 * h)
+            assert abs(fd - grad[idx]) <= 1e-4 * max(1.0, abs(grad[idx])), (idx, fd, grad[idx])
