@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(const __grid_con
       const int wr = max(wl[rr], __shfl_xor_sync(0xffffffffu, wl[rr], 16));
       const float* xr = a.x + (size_t)min(rh + rr, a.n_rows - 1) * a.len;
       float mx = -INFINITY, sum = 0.f;
+      // both sweeps run for every lane (the two halves own different rows and sync per warp)
       for (int sweep = 0; sweep < 2; ++sweep) {
+        const float mref = (sweep == 1 && mx == -INFINITY) ? 0.f : mx;   // empty: all terms 0
         for (int m0 = 0; m0 < wr; m0 += 32) {
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
@@ -335,11 +337,10 @@ __global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(const __grid_con
             if (sweep == 0)
               mx = fmaxf(mx, e);
             else
-              sum += ex2(e - mx);
+              sum += ex2(e - mref);
           }
           __syncwarp();
         }
-        if (mx == -INFINITY) break;
       }
       if (alpha[rr] != -INFINITY && mx != -INFINITY) out[rr] = mx + log2f(sum);
     }
