@@ -64,14 +64,23 @@ def _trapezoid_operator(n_r, n_c, dx):
     return Op
 
 
+def _log_mass(m):
+    """log m with log 0 = -inf and no gradient through zero-mass pixels: the loss sees such a
+    pixel only through exp(f/eps) = m exp(-S), which is linear in m = amp^2 / sum amp^2, so
+    its derivative with respect to the amplitude is 0 there."""
+    pos = m > 0
+    safe = torch.where(pos, m, torch.ones_like(m))
+    return torch.where(pos, torch.log(safe), torch.full_like(m, -math.inf))
+
+
 def phase_loss(g, G, eps, iters, w, phi_target, dx):
     """L(g, G) for torch float64 tensors g, G (n_r x n_c, requires_grad allowed)."""
     n_r, n_c = g.shape
     C = _cost(n_r, n_c)
     a = (g * g) / (g * g).sum()
     b = (G * G) / (G * G).sum()
-    la = torch.log(a).reshape(-1)
-    lb = torch.log(b).reshape(-1)
+    la = _log_mass(a).reshape(-1)
+    lb = _log_mass(b).reshape(-1)
     psi = torch.full((n_r * n_c,), eps * math.log(1.0 / (n_r * n_c)), dtype=T64)
     S = None
     for _ in range(iters):

@@ -283,3 +283,37 @@ def test_p12_adjoint_oracle_vs_finite_differences():
                 fd = (adjoint.loss_value(g, p, eps, iters, w, phi_t, dx)
                       - adjoint.loss_value(g, m, eps, iters, w, phi_t, dx)) / (2 * h)
             assert abs(fd - grad[idx]) <= 1e-4 * max(1.0, abs(grad[idx])), (idx, fd, grad[idx])
+
+
+# P12b: zero-mass pixels.  The loss sees a pixel of zero mass only through exp(f/eps) =
+# a exp(-S), linear in a = amp^2 / sum amp^2, so its one-sided derivative at amp = 0 is 0;
+# elsewhere the gradient still matches central differences, and nothing is NaN.
+def test_p12b_adjoint_oracle_with_zero_masses():
+    from oracle import adjoint
+    rng = np.random.default_rng(13)
+    n_r, n_c = 6, 7
+    g = rng.uniform(0.3, 1.0, size=(n_r, n_c))
+    G = rng.uniform(0.3, 1.0, size=(n_r, n_c))
+    g[1, 2] = g[4, 6] = 0.0
+    G[0, 0] = G[3, 3] = G[5, 1] = 0.0
+    eps, iters, dx = 1.5, 6, 1 / math.sqrt(7)
+    w = rng.uniform(0, 1, size=(n_r, n_c))
+    phi_t = rng.normal(0, 0.1, size=(n_r, n_c))
+    L, dg, dG = adjoint.gradients(g, G, eps, iters, w, phi_t, dx)
+    assert np.isfinite(dg).all() and np.isfinite(dG).all()
+    assert dg[1, 2] == 0.0 and dg[4, 6] == 0.0
+    assert dG[0, 0] == 0.0 and dG[3, 3] == 0.0 and dG[5, 1] == 0.0
+    h = 1e-3
+    for (arr, grad) in ((g, dg), (G, dG)):
+        for idx in [(0, 1), (2, 2), (5, 6)]:
+            p = arr.copy(); p[idx] += h
+            m = arr.copy(); m[idx] -= h
+            args_p = (p, G) if arr is g else (g, p)
+            args_m = (m, G) if arr is g else (g, m)
+            fd = (adjoint.loss_value(*args_p, eps, iters, w, phi_t, dx)
+                  - adjoint.loss_value(*args_m, eps, iters, w, phi_t, dx)) / (2 * h)
+            assert abs(fd - grad[idx]) <= 1e-4 * max(1.0, abs(grad[idx])), (idx, fd, grad[idx])
+    # one-sided difference at a zero-mass pixel: L(h) - L(0) = O(h^2)
+    p = g.copy(); p[1, 2] = h
+    d1 = adjoint.loss_value(p, G, eps, iters, w, phi_t, dx) - L
+    assert abs(d1) <= 10 * h * h * max(1.0, abs(L)), d1
