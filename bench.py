@@ -175,6 +175,60 @@ FFMA_FLOP_PER_CLK_PER_SM = 256
 N_SM = 152
 
 
+def _roofline(n, a, ktimes, work, loop_ms):
+    """Roofline of the dominant kernel (largest device time in the timed loops): its
+    algorithmic work over the CUDA-event time of its own launches, against the unit that
+    bounds it.  work = per-step terms by class (banded GEMM, exact window, tensor, dense)."""
+    peaks, peak_src = _peaks()
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    steps = a.steps
+    total_ms = sum(t for t, _ in ktimes.values())
+    kernels = {k: {"ms_per_step": t / steps, "launches_per_step": c / steps,
+                   "share": t / total_ms if total_ms else None}
+               for k, (t, c) in ktimes.items() if c}
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    t_ms, n_launch = ktimes[dom]
+    sec = t_ms * 1e-3
+    gemm, exact, tensor, dense = (w * steps for w in work)
+    dense -= 2.0 * n * n * n * steps            # the phase step's two moment passes (not in the loop)
+    ex2_peak = EX2_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
+    ffma_peak = FFMA_FLOP_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
+    if dom == "band_pass_kernel[gemm]":
+        roof = {"bound": "alu", "achieved": 2.0 * gemm / sec / 1e12, "peak": ffma_peak,
+                "unit": "TFLOP/s", "work": "2 flop (one FFMA) per window term of the tilted GEMM",
+                "peak_source": f"FP32 FFMA {FFMA_FLOP_PER_CLK_PER_SM} flop/clk/SM x {N_SM} SMs x "
+                               f"{clk_mhz:.0f} MHz"}
+    elif dom == "band_pass_kernel[exact]":
+        roof = {"bound": "alu", "achieved": exact / sec / 1e12, "peak": ex2_peak, "unit": "Tex2/s",
+                "work": "one exponential per window term",
+                "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz"}
+    elif dom == "tc_pass_kernel":
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        roof = {"bound": "tensor", "achieved": 6.0 * tensor / sec / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "work": "3 BF16 multiply-adds (split precision) per tensor-core term",
+                "peak_source": "cuBLAS bf16 sustained, " + peak_src,
+                "cuda_core_terms_in_kernel": (gemm + exact) / steps}
+    elif dom == "axis_pass_kernel":
+        roof = {"bound": "alu", "achieved": dense / sec / 1e12, "peak": ex2_peak, "unit": "Tex2/s",
+                "work": "one exponential per (row, output, term) of the dense pass",
+                "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz"}
+    else:                                        # window plan: reads the row, writes the plan
+        nbytes = n_launch * (n * n * 4 + n * ((n + 15) // 16) * 12)
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peak, "unit": "GB/s",
+                "work": "x read once + 3 plan words per (row, tile) written",
+                "peak_source": "STREAM copy, " + peak_src}
+    roof.update({"kernel": dom, "frac": roof["achieved"] / roof["peak"], "traffic": None,
+                 "launches": n_launch, "avg_launch_us": t_ms * 1e3 / max(n_launch, 1),
+                 "kernels": kernels, "loop_ms": loop_ms,
+                 "dense_equivalent_tflops": 2.0 * 4.0 * a.iters * n ** 3 / (loop_ms * 1e-3) / 1e12,
+                 "terms_per_iter": {"band_gemm": work[0] / a.iters, "band_exact": work[1] / a.iters,
+                                    "tensor": work[2] / a.iters,
+                                    "dense_loop": max(work[3] - 2.0 * n ** 3, 0.0) / a.iters,
+                                    "dense_equivalent": 4.0 * n ** 3}})
+    return roof
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -202,6 +256,9 @@ def run_gpu(a):
         B.fot_solve(ctx, g, G, eps, a.iters)
         B._check(B._lib.fot_phase(ctx._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
 
+    # per-kernel-class CUDA events inside the loop (the roofline's kernel durations); on for the
+    # warm-up too, so that the events exist before the timed region
+    B.fot_set_kernel_timing(ctx, True)
     for _ in range(a.warmup):
         flush.zero_()
         step()
@@ -209,9 +266,10 @@ def run_gpu(a):
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    B.fot_kernel_times(ctx)                 # drop the warm-up sums
     clocks = _Clocks(dev)
     l0 = B.fot_launch_count(ctx)
-    w0, wt0 = B.fot_work_count(ctx, tensor=True)
+    split0 = B.fot_work_split(ctx)
     torch.cuda.synchronize()
     evs = []
     loop_ms = []
@@ -231,9 +289,10 @@ def run_gpu(a):
         dist.barrier()
     torch.cuda.synchronize()
     launches = B.fot_launch_count(ctx) - l0
-    w1, wt1 = B.fot_work_count(ctx, tensor=True)
-    terms_per_step = (w1 - w0) / a.steps
-    tensor_terms_per_step = (wt1 - wt0) / a.steps
+    ktimes = B.fot_kernel_times(ctx)
+    B.fot_set_kernel_timing(ctx, False)
+    split1 = B.fot_work_split(ctx)
+    work = [(b - a_) / a.steps for a_, b in zip(split0, split1)]   # per step, by class
     clk = clocks.stop()
     step_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / a.steps
     if ws > 1:
@@ -245,47 +304,8 @@ def run_gpu(a):
     line = None
     if rank == 0:
         l1, dual = B.fot_marginal_error(ctx)
-        # roofline of the dominant kernel group: the Sinkhorn loop runs only axis passes (and,
-        # for the banded form, their chunk-maximum pre-pass); its time over the terms evaluated
         loop = statistics.median(loop_ms)
-        loop_terms = terms_per_step - 0.0
-        peaks, peak_src = _peaks()
-        clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        dense_terms = 4.0 * a.iters * n * n * n           # every (row, output, term) of 4n passes
-        if a.precision == "mixed":
-            # tensor pipe: each window term is three BF16 multiply-adds (split precision)
-            peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
-            achieved = 6.0 * tensor_terms_per_step / (loop * 1e-3) / 1e12
-            loop_terms = terms_per_step - 2.0 * n * n * n
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "kernel": "tc_pass_kernel (tcgen05 split-BF16 window GEMM) + banded CUDA-core tail",
-                    "peak_source": "cuBLAS bf16 sustained (MEASURED_PEAKS.json)",
-                    "tensor_share_of_terms": tensor_terms_per_step / max(loop_terms, 1.0),
-                    "executed_terms_per_iter": loop_terms / a.iters,
-                    "dense_terms_per_iter": dense_terms / a.iters,
-                    "dense_equivalent_tflops": 2.0 * dense_terms / (loop * 1e-3) / 1e12}
-        elif a.precision == "fp32_dense":
-            achieved = dense_terms / (loop * 1e-3) / 1e12  # Tex2/s: one exponential per term
-            peak = EX2_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tex2/s",
-                    "kernel": "axis_pass_kernel (dense exact FP32 log-sum-exp pass)",
-                    "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz"}
-        else:
-            # executed multiply-adds of the window GEMMs (2 flop per term); the loop of one
-            # step evaluates the 200 iterations' terms (the phase step is outside the loop)
-            loop_terms = terms_per_step - 2.0 * n * n * n   # phase: two dense moment passes
-            achieved = 2.0 * loop_terms / (loop * 1e-3) / 1e12
-            peak = FFMA_FLOP_PER_CLK_PER_SM * N_SM * clk_mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "kernel": "band_pass_kernel + chunk_max_kernel (banded FP32 axis passes)",
-                    "peak_source": f"FP32 FFMA {FFMA_FLOP_PER_CLK_PER_SM} flop/clk/SM x {N_SM} SMs x "
-                                   f"{clk_mhz:.0f} MHz",
-                    "executed_terms_per_iter": loop_terms / a.iters,
-                    "dense_terms_per_iter": dense_terms / a.iters,
-                    "dense_equivalent_tflops": 2.0 * dense_terms / (loop * 1e-3) / 1e12}
-        roof.update({"frac": roof["achieved"] / roof["peak"], "traffic": None,
-                     "loop_ms": loop, "pass_ms": loop / max(passes, 1),
-                     "peak_file": peak_src})
+        roof = _roofline(n, a, ktimes, work, loop)
         # end to end through the C ABI with host buffers (H2D of g, G and D2H of phi per step)
         gh = torch.from_numpy(w.g.astype(np.float32)).pin_memory()
         Gh = torch.from_numpy(w.G.astype(np.float32)).pin_memory()

@@ -222,9 +222,8 @@ fot_status fot_solve_phase_host(fot_ctx* ctx, const float* g_host, const float* 
 int64_t fot_launch_count(const fot_ctx* ctx);
 
 /* Device time (CUDA events on the context stream) of the Sinkhorn loop of the last
- * fot_solve / fot_resume, and the number of axis-pass kernels it launched (4 per iteration
- * on the FP32 path).  Only axis passes run inside that loop, so ms / passes is their mean
- * duration.  Synchronises with the end of the loop. */
+ * fot_solve / fot_resume, and the number of kernels it launched (only axis-pass kernels and
+ * their window plans run inside that loop).  Synchronises with the end of the loop. */
 fot_status fot_loop_time(fot_ctx* ctx, double* ms_out, int64_t* passes_out);
 
 /* Number of (row, output, summation index) terms the axis passes of this context have
@@ -233,6 +232,35 @@ fot_status fot_loop_time(fot_ctx* ctx, double* ms_out, int64_t* passes_out);
  * NULL) receives the part computed on the tensor cores (each term there is three BF16
  * multiply-adds of the split-precision product).  Synchronising. */
 fot_status fot_work_count(fot_ctx* ctx, int64_t* terms_out, int64_t* tensor_terms_out);
+
+/* The same count split by where the terms were evaluated: out4[0] banded tilted-GEMM items
+ * (CUDA-core FFMA), out4[1] banded exact-window items (one exponential per term), out4[2]
+ * tensor cores, out4[3] dense exact passes (including the phase step's moment passes).
+ * Synchronising.  The paper has no counterpart: a measurement aid. */
+fot_status fot_work_split(fot_ctx* ctx, int64_t* out4);
+
+/* Kernel classes of fot_kernel_times. */
+enum {
+  FOT_KERNEL_PLAN = 0,        /* window plan of a banded pass */
+  FOT_KERNEL_BAND_GEMM = 1,   /* banded pass, tilted-GEMM items (CUDA cores) */
+  FOT_KERNEL_BAND_EXACT = 2,  /* banded pass, exact-window items */
+  FOT_KERNEL_TENSOR = 3,      /* tensor-core banded pass */
+  FOT_KERNEL_DENSE = 4,       /* dense exact pass */
+  FOT_KERNEL_CLASSES = 5
+};
+
+/* Per-kernel timing of the Sinkhorn loop (a measurement aid; the paper has no counterpart).
+ * With on != 0, every kernel the loop of later fot_solve / fot_resume calls launches is
+ * bracketed by a pair of CUDA events on the context stream (a few microseconds of host time
+ * per launch; the events are created on first use and reused).  on = 0 synchronises the
+ * stream and releases the events.  Not for calls captured into a CUDA graph. */
+fot_status fot_set_kernel_timing(fot_ctx* ctx, int on);
+
+/* Device time (ms) and launch count per kernel class (arrays of FOT_KERNEL_CLASSES) over
+ * every loop since timing was switched on or last read; resets the sums.  FOT_ESTATE when
+ * timing is off, FOT_ECUDA when an event could not be created or recorded (the sums are
+ * then dropped).  Synchronising. */
+fot_status fot_kernel_times(fot_ctx* ctx, double* ms_out, int64_t* launches_out);
 
 const char* fot_status_string(fot_status s);
 

@@ -25,6 +25,10 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 FOT_FP32, FOT_MIXED, FOT_FP32_DENSE, FOT_AUTO = 0, 1, 2, 3
 FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
+FOT_KERNEL_PLAN, FOT_KERNEL_BAND_GEMM, FOT_KERNEL_BAND_EXACT, FOT_KERNEL_TENSOR, FOT_KERNEL_DENSE = 0, 1, 2, 3, 4
+FOT_KERNEL_CLASSES = 5
+KERNEL_CLASS_NAMES = ("band_plan_kernel", "band_pass_kernel[gemm]", "band_pass_kernel[exact]",
+                      "tc_pass_kernel", "axis_pass_kernel")
 STATUS = {0: "FOT_OK", 1: "FOT_EINVAL", 2: "FOT_ENOMEM", 3: "FOT_ECUDA", 4: "FOT_ENONFINITE",
           5: "FOT_ETIMEOUT", 6: "FOT_EMASS", 7: "FOT_EUNSUPPORTED", 8: "FOT_ESTATE"}
 
@@ -54,6 +58,9 @@ _SIGS = {
     "fot_launch_count": (ctypes.c_int64, [_P]),
     "fot_loop_time": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
     "fot_work_count": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "fot_work_split": (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "fot_set_kernel_timing": (_I, [_P, _I]),
+    "fot_kernel_times": (_I, [_P, _DP, ctypes.POINTER(ctypes.c_int64)]),
     "fot_status_string": (ctypes.c_char_p, [_I]),
     "fot_backward": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "fot_batch_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _I, _I, _P]),
@@ -260,6 +267,25 @@ def fot_work_count(ctx, tensor=False):
     n, t = ctypes.c_int64(), ctypes.c_int64()
     _check(_lib.fot_work_count(ctx._h, ctypes.byref(n), ctypes.byref(t)), "fot_work_count")
     return (n.value, t.value) if tensor else n.value
+
+
+def fot_work_split(ctx):
+    """(banded GEMM, exact-window, tensor-core, dense) terms since creation."""
+    out = (ctypes.c_int64 * 4)()
+    _check(_lib.fot_work_split(ctx._h, out), "fot_work_split")
+    return tuple(int(v) for v in out)
+
+
+def fot_set_kernel_timing(ctx, on):
+    _check(_lib.fot_set_kernel_timing(ctx._h, 1 if on else 0), "fot_set_kernel_timing")
+
+
+def fot_kernel_times(ctx):
+    """{class name: (ms, launches)} over the loops since timing was switched on / last read."""
+    ms = (ctypes.c_double * FOT_KERNEL_CLASSES)()
+    n = (ctypes.c_int64 * FOT_KERNEL_CLASSES)()
+    _check(_lib.fot_kernel_times(ctx._h, ms, n), "fot_kernel_times")
+    return {KERNEL_CLASS_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(FOT_KERNEL_CLASSES)}
 
 
 class _View(Context):

@@ -201,9 +201,13 @@ extern "C" fot_status fot_backward(fot_ctx* c, const float* g, const float* G, c
   cudaStream_t s = c->stream;
   // device memory of the backward: checkpoints, one segment, adjoints and temporaries
   std::vector<float*> bufs;
+  int failed = 0;
   auto alloc = [&](size_t words) -> float* {
     float* p = nullptr;
-    if (cudaMalloc((void**)&p, words * sizeof(float)) != cudaSuccess) return nullptr;
+    if (cudaMalloc((void**)&p, words * sizeof(float)) != cudaSuccess) {
+      ++failed;
+      return nullptr;
+    }
     bufs.push_back(p);
     return p;
   };
@@ -232,9 +236,7 @@ extern "C" fot_status fot_backward(fot_ctx* c, const float* g, const float* G, c
   float* lyn = alloc(N);
   float* pp = alloc(N);
   float* pn = alloc(N);
-  bool ok = true;
-  for (float* p : bufs) ok = ok && p;
-  ok = ok && bufs.size() == 24;
+  const bool ok = failed == 0;
   auto cleanup = [&]() {
     cudaStreamSynchronize(s);
     for (float* p : bufs)

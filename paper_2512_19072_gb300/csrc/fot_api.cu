@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "fot_common.cuh"
@@ -22,7 +23,7 @@ void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi
 void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, float* phi);
 void c_transform_envelope(fot_ctx* c, const float* pot_in, float* out);
 void half_step_band(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
-                    float* pot_out, float* logsum, float* tmp, float* cmax);
+                    float* pot_out, float* logsum, float* tmp);
 // tensor-core path (fot_tc.cu)
 bool tc_supported(int rows, int cols);
 int tc_create(fot_ctx* c);
@@ -35,6 +36,41 @@ int64_t tc_terms(fot_ctx* c);
 using namespace fot;
 
 static const int kMaxDim = 4096;
+
+namespace fot {
+thread_local KernelTimer* g_ktimer = nullptr;
+
+void ktimer_begin(cudaStream_t s, int cls) {
+  KernelTimer* t = g_ktimer;
+  if (!t || t->failed) return;
+  const size_t need = 2 * (t->used + 1);
+  while (t->ev.size() < need) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      t->failed = true;
+      return;
+    }
+    t->ev.push_back(e);
+  }
+  if (t->cls.size() < t->used + 1) t->cls.resize(t->used + 1);
+  t->cls[t->used] = cls;
+  if (cudaEventRecord(t->ev[2 * t->used], s) != cudaSuccess) t->failed = true;
+}
+
+void ktimer_end(cudaStream_t s) {
+  KernelTimer* t = g_ktimer;
+  if (!t || t->failed) return;
+  if (cudaEventRecord(t->ev[2 * t->used + 1], s) != cudaSuccess) t->failed = true;
+  ++t->used;
+}
+}  // namespace fot
+
+static void ktimer_free(fot_ctx* c) {
+  if (!c->ktimer) return;
+  for (cudaEvent_t e : c->ktimer->ev) cudaEventDestroy(e);
+  delete c->ktimer;
+  c->ktimer = nullptr;
+}
 
 #define FOT_CUDA(call)                                \
   do {                                                \
@@ -115,15 +151,13 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   bool ok = true;
   for (float** b : bufs) ok = ok && cudaMalloc((void**)b, N * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->col_phi, (size_t)rows * sizeof(float)) == cudaSuccess;
-  // chunk maxima of both passes' inputs (32-wide chunks), then the per-(row, 16-output tile)
-  // plan of the larger pass (3 words each)
+  // the per-(row, 16-output tile) plan of the larger banded pass (3 words each)
   const size_t plan_words = 3 * std::max((size_t)rows * ((cols + 15) / 16), (size_t)cols * ((rows + 15) / 16));
-  const size_t nchunk = (size_t)rows * ((cols + 31) / 32) + (size_t)cols * ((rows + 31) / 32) + plan_words;
-  ok = ok && cudaMalloc((void**)&c->cmax, nchunk * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->plan, plan_words * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->red, (size_t)(4 * c->red_blocks + 16) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
-  ok = ok && cudaMalloc((void**)&c->terms, sizeof(unsigned long long)) == cudaSuccess;
-  if (ok) ok = cudaMemsetAsync(c->terms, 0, sizeof(unsigned long long), c->stream) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&c->terms, 2 * sizeof(unsigned long long)) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(c->terms, 0, 2 * sizeof(unsigned long long), c->stream) == cudaSuccess;
   if (ok) ok = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) == cudaSuccess;
   if (ok) ok = cudaEventCreate(&c->ev_loop0) == cudaSuccess && cudaEventCreate(&c->ev_loop1) == cudaSuccess;
   if (ok && precision == FOT_MIXED) {
@@ -147,8 +181,9 @@ void fot_destroy(fot_ctx* c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->tc) tc_destroy(c);
+  ktimer_free(c);
   float* bufs[] = {c->la, c->lb, c->f, c->psi, c->R, c->R2, c->S_last, c->tmp, c->tmp2, c->phi,
-                   c->col_phi, c->cmax};
+                   c->col_phi, c->plan};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (c->red) cudaFree(c->red);
@@ -170,12 +205,66 @@ int64_t fot_launch_count(const fot_ctx* c) { return c ? c->launches : -1; }
 fot_status fot_work_count(fot_ctx* c, int64_t* terms_out, int64_t* tensor_terms_out) {
   if (!c || !terms_out) return FOT_EINVAL;
   FOT_CUDA(cudaSetDevice(c->device));
-  unsigned long long t = 0;
-  FOT_CUDA(cudaMemcpyAsync(&t, c->terms, sizeof(t), cudaMemcpyDeviceToHost, c->stream));
+  int64_t w[4];
+  const fot_status s = fot_work_split(c, w);
+  if (s != FOT_OK) return s;
+  *terms_out = w[0] + w[1] + w[2] + w[3];
+  if (tensor_terms_out) *tensor_terms_out = w[2];
+  return FOT_OK;
+}
+
+fot_status fot_work_split(fot_ctx* c, int64_t* out4) {
+  if (!c || !out4) return FOT_EINVAL;
+  FOT_CUDA(cudaSetDevice(c->device));
+  unsigned long long t[2] = {0, 0};
+  FOT_CUDA(cudaMemcpyAsync(t, c->terms, sizeof(t), cudaMemcpyDeviceToHost, c->stream));
   FOT_CUDA(cudaStreamSynchronize(c->stream));
-  const int64_t tt = c->tc ? tc_terms(c) : 0;
-  *terms_out = (int64_t)t + c->host_terms + tt;
-  if (tensor_terms_out) *tensor_terms_out = tt;
+  out4[0] = (int64_t)t[0];
+  out4[1] = (int64_t)t[1];
+  out4[2] = c->tc ? tc_terms(c) : 0;
+  out4[3] = c->host_terms;
+  return FOT_OK;
+}
+
+fot_status fot_set_kernel_timing(fot_ctx* c, int on) {
+  if (!c) return FOT_EINVAL;
+  if (!on) {
+    if (c->ktimer) {
+      FOT_CUDA(cudaSetDevice(c->device));
+      FOT_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    ktimer_free(c);
+    return FOT_OK;
+  }
+  if (!c->ktimer) {
+    c->ktimer = new (std::nothrow) KernelTimer();
+    if (!c->ktimer) return FOT_ENOMEM;
+  }
+  return FOT_OK;
+}
+
+fot_status fot_kernel_times(fot_ctx* c, double* ms_out, int64_t* launches_out) {
+  if (!c || !ms_out || !launches_out) return FOT_EINVAL;
+  for (int k = 0; k < kKClasses; ++k) {
+    ms_out[k] = 0.0;
+    launches_out[k] = 0;
+  }
+  KernelTimer* t = c->ktimer;
+  if (!t) return FOT_ESTATE;
+  FOT_CUDA(cudaSetDevice(c->device));
+  if (t->failed) {
+    t->used = 0;
+    t->failed = false;
+    return FOT_ECUDA;
+  }
+  if (t->used) FOT_CUDA(cudaEventSynchronize(t->ev[2 * t->used - 1]));
+  for (size_t i = 0; i < t->used; ++i) {
+    float ms = 0.f;
+    FOT_CUDA(cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]));
+    ms_out[t->cls[i]] += ms;
+    launches_out[t->cls[i]] += 1;
+  }
+  t->used = 0;
   return FOT_OK;
 }
 
@@ -208,11 +297,12 @@ static void half_step(fot_ctx* c, const float* pot_in, const float* lmarg, doubl
   else if (c->precision == FOT_FP32_DENSE)
     half_step_simt(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
   else
-    half_step_band(c, pot_in, lmarg, eps, pot_out, logsum, c->R, c->cmax);
+    half_step_band(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
 }
 
 static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int units, int iters) {
   const int64_t l0 = c->launches;
+  g_ktimer = c->ktimer;                    // null unless kernel timing is on
   cudaEventRecord(c->ev_loop0, c->stream);
   for (int t = 0; t < iters; ++t) {
     const double e = eps_px(c, eps[n_eps == 1 ? 0 : t], units);
@@ -224,6 +314,7 @@ static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int u
     c->sched.push_back(e);
   }
   cudaEventRecord(c->ev_loop1, c->stream);
+  g_ktimer = nullptr;
   c->loop_passes = c->launches - l0;
   if (iters > 0) c->have_solution = true;
   return check_launch(c);

@@ -10,15 +10,14 @@ namespace fot {
 // (row, 16-output tile), n_rows * n_tiles words each, consecutive.
 struct BandArgs {
   const float* x;      // [n_rows][len] input
-  float* cmax;         // [n_rows][n_chunks] chunk maxima of x * x_scale (log2 units)
   float* plan;
   const float* lmarg;  // potential-update mode: natural log marginal, layout of y
   float* y;            // [len][n_rows] output (transposed)
   float* logsum;       // potential-update mode: optional natural-log LSE, layout of y
   int* err;
-  unsigned long long* terms;     // += (row, output, m) triples evaluated on the CUDA cores
+  unsigned long long* terms;     // [2]: += (row, output, m) triples evaluated on the CUDA cores,
+                                 // [0] tilted-GEMM items, [1] exact-window items
   unsigned long long* tc_terms;  // += triples evaluated on the tensor cores
-  unsigned char* skip;           // per (128-row block, tile): taken by the tensor kernel
   float x_scale, c, eps;
   int n_rows, len, n_chunks, n_tiles;
   int row_base, plan_base, item_base, cta_base;   // first global work index of each kernel
@@ -35,7 +34,7 @@ struct BandTable {
   BandArgs p[MAXP];
 };
 
-// problem owning global work index gi of kind WHICH (0 rows, 1 plan warps, 2 band items,
+// problem owning global work index gi of kind WHICH (0 rows, 1 plan CTAs (one per row), 2 band items,
 // 3 tensor CTAs): binary search over the prefix sums (a single problem needs none)
 template <int MAXP, int WHICH>
 __device__ __forceinline__ int find_prob(const BandTable<MAXP>& t, int gi) {
@@ -57,17 +56,18 @@ __device__ __forceinline__ int find_prob(const BandTable<MAXP>& t, int gi) {
 template <int MAXP>
 void band_table_finish(BandTable<MAXP>& t);
 
-// chunk maxima and per-(row, tile) plan of every problem
+// per-(row, tile) plan of every problem
 template <int MAXP>
 void band_prepare(cudaStream_t s, const BandTable<MAXP>& t);
 
-// the CUDA-core window sums; items whose (128-row block, tile) is marked in skip are left
-// alone (MODE 0: log-sum output; MODE 1: potential update)
+// the CUDA-core window sums (MODE 0: log-sum output; MODE 1: potential update)
 template <int MODE, int MAXP>
 void band_simt(cudaStream_t s, const BandTable<MAXP>& t);
 
-// the tensor-core window sums (fot_tc.cu); marks skip for the tiles it takes
+// the tensor-core window sums (fot_tc.cu); tiles outside its tilt bound take the CUDA-core
+// sums inside the same kernel, and a pass where no tile can meet the bound runs band_simt.
+// Returns the number of kernels launched.
 template <int MODE, int MAXP>
-void tc_pass(cudaStream_t s, const BandTable<MAXP>& t);
+int tc_pass(cudaStream_t s, const BandTable<MAXP>& t);
 
 }  // namespace fot

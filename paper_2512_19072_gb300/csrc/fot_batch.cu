@@ -1,8 +1,8 @@
 // Batched solve: many independent beam-shaping problems of different grid sizes in one
 // stream of multi-problem launches.
 //
-// Every axis pass of every problem goes into the same four launches (chunk maxima, window
-// plan, the two banded window-sum kernels; plus the tensor-core kernel for the mixed form):
+// Every axis pass of every problem goes into the same three launches (window plan and the two
+// banded window-sum kernels; window plan and the tensor-core kernel for the mixed form):
 // the kernels take a table of up to 64 problems by value and map each warp / CTA to its
 // problem by prefix sums (BandTable).  The whole solve - problem setup and all iterations
 // with each iteration's eps baked into its launches - is captured once into a CUDA graph and
@@ -24,7 +24,6 @@ namespace fot {
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 int tc_create(fot_ctx* c);
-unsigned char* tc_done(fot_ctx* c);
 unsigned long long* tc_terms_ptr(fot_ctx* c);
 }  // namespace fot
 
@@ -73,22 +72,27 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         a2.y = pout;
         a2.lmarg = half == 0 ? c->la : c->lb;
         a2.logsum = (half == 0 && it == iters - 1) ? c->S_last : nullptr;
-        if (use_tc) {
-          a1.skip = a2.skip = tc_done(c);
-          a1.tc_terms = a2.tc_terms = tc_terms_ptr(c);
-        }
+        if (use_tc) a1.tc_terms = a2.tc_terms = tc_terms_ptr(c);
         t1->p[q] = a1;
         t2->p[q] = a2;
       }
       band_table_finish(*t1);
       band_table_finish(*t2);
       band_prepare(st, *t1);
-      if (use_tc) tc_pass<0>(st, *t1);
-      band_simt<0>(st, *t1);
+      if (use_tc) {
+        k += tc_pass<0>(st, *t1);
+      } else {
+        band_simt<0>(st, *t1);
+        k += 2;
+      }
       band_prepare(st, *t2);
-      if (use_tc) tc_pass<1>(st, *t2);
-      band_simt<1>(st, *t2);
-      k += use_tc ? 10 : 8;
+      if (use_tc) {
+        k += tc_pass<1>(st, *t2);
+      } else {
+        band_simt<1>(st, *t2);
+        k += 2;
+      }
+      k += 2;                                             // the two plan launches
     }
   }
   delete t1;

@@ -29,6 +29,29 @@ __device__ __forceinline__ bool error_latched(const int* err) {
   return *(volatile const int*)err != 0;
 }
 
+// Optional per-kernel-class timing of the Sinkhorn loop (fot_set_kernel_timing): while a
+// context with timing on runs its loop, g_ktimer points at its timer and every launch site
+// brackets its kernel with a pair of events; fot_kernel_times sums them per class.
+enum KernelClass : int {
+  kKPlan = FOT_KERNEL_PLAN,             // band_plan_kernel
+  kKBandGemm = FOT_KERNEL_BAND_GEMM,    // band_pass_kernel, tilted-GEMM items
+  kKBandExact = FOT_KERNEL_BAND_EXACT,  // band_pass_kernel, exact-window items
+  kKTensor = FOT_KERNEL_TENSOR,         // tc_pass_kernel
+  kKDense = FOT_KERNEL_DENSE,           // axis_pass_kernel (dense exact pass)
+  kKClasses = FOT_KERNEL_CLASSES
+};
+
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;   // (start, end) pairs, created on first use and reused
+  std::vector<int> cls;          // class of each pair
+  size_t used = 0;               // pairs recorded since the last read
+  bool failed = false;           // an event could not be created or recorded
+};
+
+extern thread_local KernelTimer* g_ktimer;
+void ktimer_begin(cudaStream_t s, int cls);   // no-op unless g_ktimer is set
+void ktimer_end(cudaStream_t s);
+
 }  // namespace fot
 
 // Context (opaque to callers).  Every device buffer is owned here.
@@ -47,10 +70,11 @@ struct fot_ctx {
   float* tmp2 = nullptr;     // rows x cols scratch
   float* phi = nullptr;      // rows x cols phase (host-buffer entry point)
   float* col_phi = nullptr;  // rows: phase along the centre column
-  float* cmax = nullptr;     // chunk maxima of a banded pass's input (rows*cols/32 + slack)
+  float* plan = nullptr;     // per-(row, 16-output tile) window plan of a banded pass, 3 words each
   double* red = nullptr;     // reduction scratch (partials + results)
   int* err = nullptr;        // latched device status
-  unsigned long long* terms = nullptr;  // device counter of evaluated (row, output, m) terms
+  unsigned long long* terms = nullptr;  // device counters of evaluated (row, output, m) terms on
+                                        // the CUDA cores: [0] banded GEMM, [1] exact windows
   int64_t host_terms = 0;    // terms of passes whose count is known on the host (dense)
   int red_blocks = 0;
   // host-side state
@@ -65,6 +89,7 @@ struct fot_ctx {
   std::vector<double> sched; // eps (px^2) of every iteration since the last fot_solve
   // mixed-precision (tensor-core) resources, owned by fot_tc.cu
   void* tc = nullptr;
+  fot::KernelTimer* ktimer = nullptr;   // per-kernel-class loop timing, when switched on
 };
 
 namespace fot {

@@ -146,7 +146,9 @@ static void launch_pass(fot_ctx* c, const PassArgs& p) {
                          227 * 1024);
     configured = true;
   }
+  ktimer_begin(c->stream, kKDense);
   axis_pass_kernel<RB, MODE><<<grid, threads, smem, c->stream>>>(p);
+  ktimer_end(c->stream);
   c->launches++;
   c->host_terms += (int64_t)p.n_rows * p.len * p.len;
 }

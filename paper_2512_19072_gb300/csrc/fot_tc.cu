@@ -15,11 +15,12 @@
 // lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
 // about 2^-16 relative per product instead of 2^-8, FP32 accumulation.
 //
-// A CTA takes its tile only when the tilt bounds of the banded pass hold for the common
-// window length W of its 128 rows; otherwise it leaves a flag at 0 and the CUDA-core
-// banded kernels compute those rows.  Every mbarrier wait is bounded: on time-out the kernel
-// latches FOT_ETIMEOUT, stops issuing, frees its tensor memory and returns.
-#include "fot_band.cuh"
+// A CTA uses the tensor cores only when the tilt bounds of the banded pass hold for the
+// common window length W of its 128 rows; otherwise its eight warps compute the tile with
+// the CUDA-core window sums of the banded pass (16 rows each).  Every mbarrier wait is
+// bounded: on time-out the kernel latches FOT_ETIMEOUT, stops issuing, frees its tensor
+// memory and returns.
+#include "fot_band_item.cuh"
 
 #include <cuda_bf16.h>
 
@@ -122,7 +123,7 @@ __device__ __forceinline__ void store_split8(const float* v, uint32_t hi_addr, u
 }
 
 template <int MODE, int MAXP>
-__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+__global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base_sh;
@@ -142,7 +143,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   const float* __restrict__ p_alpha = a.plan;
   const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
   const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
-  unsigned char* done = a.skip;
   unsigned long long* tc_terms = a.tc_terms;
 
   // per-row plan and the common window length
@@ -166,8 +166,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   const int W = ((s_wmax + kKC - 1) / kKC) * kKC;
   const float kmax = (float)(kTN / 2);
   const bool take = s_wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
-  if (tid == 0) done[(size_t)blk * a.n_tiles + tile] = take ? 1 : 0;
-  if (!take) return;                                    // CTA-uniform
+  if (!take) {                                          // CTA-uniform
+    const int rw = r0 + warp * 2 * kBR;                 // this warp's 16 rows
+    if (rw < a.n_rows) {
+      float* sAw = reinterpret_cast<float*>(smem) + warp * 2 * kSA;
+      band_item<MODE, 0>(a, rw, tile, sAw);
+      band_item<MODE, 1>(a, rw, tile, sAw);
+    }
+    return;
+  }
   if (tid == 0) atomicAdd(tc_terms, (unsigned long long)W * kTN * kTM);
 
   // tensor memory for the 128 x 32 FP32 accumulator, and the two stage barriers
@@ -356,9 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 }
 
 struct TcState {
-  unsigned char* done = nullptr;          // per (128-row block, tile): taken by the tensor kernel
   unsigned long long* tc_terms = nullptr; // window terms computed on the tensor cores
-  size_t n_done = 0;
 };
 
 }  // namespace
@@ -368,13 +373,9 @@ bool tc_supported(int rows, int cols) { return rows >= 1 && cols >= 1; }
 int tc_create(fot_ctx* c) {
   TcState* t = new (std::nothrow) TcState();
   if (!t) return 1;
-  const size_t a = (size_t)((c->rows + kTM - 1) / kTM) * ((c->cols + kTN - 1) / kTN);
-  const size_t b = (size_t)((c->cols + kTM - 1) / kTM) * ((c->rows + kTN - 1) / kTN);
-  t->n_done = a > b ? a : b;
-  if (cudaMalloc((void**)&t->done, t->n_done) != cudaSuccess ||
-      cudaMalloc((void**)&t->tc_terms, sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMalloc((void**)&t->tc_terms, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemsetAsync(t->tc_terms, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
-    if (t->done) cudaFree(t->done);
+    if (t->tc_terms) cudaFree(t->tc_terms);
     delete t;
     return 1;
   }
@@ -383,7 +384,6 @@ int tc_create(fot_ctx* c) {
       cudaFuncSetAttribute(tc_pass_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
       cudaFuncSetAttribute(tc_pass_kernel<0, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
       cudaFuncSetAttribute(tc_pass_kernel<1, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
-    cudaFree(t->done);
     cudaFree(t->tc_terms);
     delete t;
     return 1;
@@ -395,7 +395,6 @@ int tc_create(fot_ctx* c) {
 void tc_destroy(fot_ctx* c) {
   TcState* t = (TcState*)c->tc;
   if (!t) return;
-  cudaFree(t->done);
   cudaFree(t->tc_terms);
   delete t;
   c->tc = nullptr;
@@ -410,22 +409,36 @@ int64_t tc_terms(fot_ctx* c) {
   return (int64_t)v;
 }
 
-template <int MODE, int MAXP>
-void tc_pass(cudaStream_t s, const BandTable<MAXP>& t) {
-  tc_pass_kernel<MODE, MAXP><<<t.ctas, kThreads, kSmemBytes, s>>>(t);
+// true when some problem of the table can meet the tilt bound: a taken tile has W >= kKC,
+// so c > kTiltMaxTC / (kTN / 2 * kKC) rules the tensor cores out for the whole pass
+template <int MAXP>
+bool tc_useful(const BandTable<MAXP>& t) {
+  for (int q = 0; q < t.n; ++q)
+    if ((float)(kTN / 2) * (float)kKC * t.p[q].c <= kTiltMaxTC) return true;
+  return false;
 }
 
-unsigned char* tc_done(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->done : nullptr; }
+template <int MODE, int MAXP>
+int tc_pass(cudaStream_t s, const BandTable<MAXP>& t) {
+  if (!tc_useful(t)) {
+    band_simt<MODE>(s, t);
+    return 2;
+  }
+  ktimer_begin(s, kKTensor);
+  tc_pass_kernel<MODE, MAXP><<<t.ctas, kThreads, kSmemBytes, s>>>(t);
+  ktimer_end(s);
+  return 1;
+}
+
 unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
-template void tc_pass<0, 1>(cudaStream_t, const BandTable<1>&);
-template void tc_pass<1, 1>(cudaStream_t, const BandTable<1>&);
-template void tc_pass<0, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
-template void tc_pass<1, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template int tc_pass<0, 1>(cudaStream_t, const BandTable<1>&);
+template int tc_pass<1, 1>(cudaStream_t, const BandTable<1>&);
+template int tc_pass<0, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template int tc_pass<1, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
 
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 
-// One half-step with the tensor-core banded passes (CUDA-core kernels take the tiles the
-// tensor kernel declines).
+// One half-step with the tensor-core banded passes.
 void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
                   float* logsum) {
   TcState* ts = (TcState*)c->tc;
@@ -433,23 +446,19 @@ void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double ep
   t.n = 1;
   t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
   t.p[0].y = c->R;
-  t.p[0].skip = ts->done;
   t.p[0].tc_terms = ts->tc_terms;
   band_table_finish(t);
   band_prepare(c->stream, t);
-  tc_pass<0>(c->stream, t);
-  band_simt<0>(c->stream, t);
+  int k = 2 + tc_pass<0>(c->stream, t);
   t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
   t.p[0].y = pot_out;
   t.p[0].lmarg = lmarg;
   t.p[0].logsum = logsum;
-  t.p[0].skip = ts->done;
   t.p[0].tc_terms = ts->tc_terms;
   band_table_finish(t);
   band_prepare(c->stream, t);
-  tc_pass<1>(c->stream, t);
-  band_simt<1>(c->stream, t);
-  c->launches += 10;
+  k += tc_pass<1>(c->stream, t);
+  c->launches += k;
 }
 
 }  // namespace fot

@@ -59,6 +59,10 @@ def test_host_side_argument_errors(lib):
     assert lib.fot_solve(None, None, None, ctypes.c_double(0), None, 1, 0, 1) == 1
     lib.fot_launch_count.restype = ctypes.c_int64
     assert lib.fot_launch_count(None) == -1
+    for name, nargs in (("fot_work_split", 1), ("fot_kernel_times", 2), ("fot_set_kernel_timing", 1)):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(None, *([None] * nargs)) == 1, name                    # FOT_EINVAL
 
 
 def test_injected_allocation_failure(lib, monkeypatch):

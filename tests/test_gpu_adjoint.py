@@ -43,6 +43,33 @@ def test_adjoint_matches_dense_oracle(fot_lib, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def test_backward_workload_at_32_matches_dense_oracle(fot_lib, prec):
+    """The backward workload's construction at 32 x 32 (two-Gaussian beam, ring/rectangle
+    target with zero-mass background, eps 4 px^2, 100 iterations, checkpoint every 10)
+    against the dense FP64 autograd gradient."""
+    B = fot_lib
+    P = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED}[prec]
+    n = 32
+    w4 = inputs.config4(n=n)
+    g, G = f32(w4.g), f32(w4.G)
+    w, phi_t = f32(w4.extra["w"]), f32(w4.extra["phi_target"])
+    dx = 1 / math.sqrt(n)
+    L_ref, dg_ref, dG_ref = adjoint.gradients(g, G, 4.0, w4.iters, w, phi_t, dx)
+    ctx = B.fot_create(n, n, P)
+    gt, Gt = to_dev(g), to_dev(G)
+    B.fot_solve(ctx, gt, Gt, w4.eps, w4.iters, dx=dx)
+    phi, _, _ = B.fot_phase(ctx)
+    dg, dG = B.fot_backward(ctx, gt, Gt, dL_dphi=_loss_seed(phi, to_dev(w), to_dev(phi_t)),
+                            checkpoint_every=10)
+    dg, dG = dg.double().cpu().numpy(), dG.double().cpu().numpy()
+    for got, ref in ((dg, dg_ref), (dG, dG_ref)):
+        assert np.isfinite(got).all()
+        assert (got[ref == 0] == 0).all()          # zero-mass pixels: derivative 0
+        assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+    ctx.close()
+
+
 def test_autograd_function_and_checkpoint_invariance(fot_lib):
     B = fot_lib
     rng = np.random.default_rng(41)

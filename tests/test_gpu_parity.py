@@ -356,8 +356,11 @@ def mixed_atol(eps):
 
 
 @pytest.mark.parametrize("shape", [(64, 64), (100, 130), (257, 200), (300, 300)])
-@pytest.mark.parametrize("eps", [60.0, 3000.0])
+@pytest.mark.parametrize("eps", [4.0, 12.0, 60.0, 3000.0])
 def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
+    """eps 4: no tile can meet the tensor kernel's tilt bound (the pass runs the CUDA-core
+    kernels); eps 12: the tensor kernel computes the tiles it declines with the CUDA-core
+    window sums inside the same launch; eps 60, 3000: mostly tensor-core tiles."""
     B = fot_lib
     rng = np.random.default_rng(hash((shape, eps, "mixed")) % 2**32)
     g, G = _masses(rng, shape, 0.15)
@@ -368,6 +371,7 @@ def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
     f_gpu, S_gpu = B.fot_u_update(ctx, to_dev(psi), eps, with_logsum=True)
     B.fot_sync(ctx)
     _, tensor_terms = B.fot_work_count(ctx, tensor=True)
+    split = B.fot_work_split(ctx)
     la = fot.log0(fot.marginal(g))
     f_ref, S_ref = fot.u_update(psi, la, eps)
     f_np = to_np(f_gpu)
@@ -377,6 +381,10 @@ def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
     assert err <= POT_RTOL * np.abs(f_ref[fin]).max() + mixed_atol(eps), (err, mixed_atol(eps))
     if eps >= 3000.0:
         assert tensor_terms > 0          # these tiles satisfy the tilt bounds: tensor cores used
+    if eps <= 12.0:
+        assert split[0] + split[1] > 0, split   # CUDA-core window sums ran
+    if eps == 4.0:
+        assert split[2] == 0, split            # no tile can meet the tilt bound at eps 4
     ctx.close()
 
 
