@@ -241,12 +241,11 @@ fot_status fot_work_split(fot_ctx* ctx, int64_t* out4);
 
 /* Kernel classes of fot_kernel_times. */
 enum {
-  FOT_KERNEL_PLAN = 0,        /* window plan of a banded pass */
-  FOT_KERNEL_BAND_GEMM = 1,   /* banded pass, tilted-GEMM items (CUDA cores) */
-  FOT_KERNEL_BAND_EXACT = 2,  /* banded pass, exact-window items */
-  FOT_KERNEL_TENSOR = 3,      /* tensor-core banded pass */
-  FOT_KERNEL_DENSE = 4,       /* dense exact pass */
-  FOT_KERNEL_CLASSES = 5
+  FOT_KERNEL_PLAN = 0,     /* window plan of a banded pass */
+  FOT_KERNEL_BAND = 1,     /* banded pass on the CUDA cores (tilted-GEMM and exact-window items) */
+  FOT_KERNEL_TENSOR = 2,   /* tensor-core banded pass */
+  FOT_KERNEL_DENSE = 3,    /* dense exact pass */
+  FOT_KERNEL_CLASSES = 4
 };
 
 /* Per-kernel timing of the Sinkhorn loop (a measurement aid; the paper has no counterpart).

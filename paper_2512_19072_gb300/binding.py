@@ -25,10 +25,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 FOT_FP32, FOT_MIXED, FOT_FP32_DENSE, FOT_AUTO = 0, 1, 2, 3
 FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
-FOT_KERNEL_PLAN, FOT_KERNEL_BAND_GEMM, FOT_KERNEL_BAND_EXACT, FOT_KERNEL_TENSOR, FOT_KERNEL_DENSE = 0, 1, 2, 3, 4
-FOT_KERNEL_CLASSES = 5
-KERNEL_CLASS_NAMES = ("band_plan_kernel", "band_pass_kernel[gemm]", "band_pass_kernel[exact]",
-                      "tc_pass_kernel", "axis_pass_kernel")
+FOT_KERNEL_PLAN, FOT_KERNEL_BAND, FOT_KERNEL_TENSOR, FOT_KERNEL_DENSE = 0, 1, 2, 3
+FOT_KERNEL_CLASSES = 4
+KERNEL_CLASS_NAMES = ("band_plan_kernel", "band_pass_kernel", "tc_pass_kernel", "axis_pass_kernel")
 STATUS = {0: "FOT_OK", 1: "FOT_EINVAL", 2: "FOT_ENOMEM", 3: "FOT_ECUDA", 4: "FOT_ENONFINITE",
           5: "FOT_ETIMEOUT", 6: "FOT_EMASS", 7: "FOT_EUNSUPPORTED", 8: "FOT_ESTATE"}
 

@@ -162,8 +162,12 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
   }
 }
 
-template <int MODE, int PATH, int MAXP>
-__global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+#ifndef FOT_BAND_MIN_BLOCKS
+#define FOT_BAND_MIN_BLOCKS 3   // resident CTAs per SM the register budget is sized for
+#endif
+
+template <int MODE, int MAXP>
+__global__ void __launch_bounds__(kBW * 32, FOT_BAND_MIN_BLOCKS) band_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   __shared__ __align__(16) float sA[kBW][2 * kSA];
   const int warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * kBW + warp;
@@ -172,7 +176,9 @@ __global__ void __launch_bounds__(kBW * 32, 3) band_pass_kernel(const __grid_con
   if (error_latched(a.err)) return;
   const int lw = gw - a.item_base;
   const int tile = lw % a.n_tiles, r0 = (lw / a.n_tiles) * 2 * kBR;
-  band_item<MODE, PATH>(a, r0, tile, sA[warp]);
+  // each item takes exactly one of the two (warp-uniform choice inside band_item)
+  band_item<MODE, 0>(a, r0, tile, sA[warp]);
+  band_item<MODE, 1>(a, r0, tile, sA[warp]);
 }
 
 template <int MAXP>
@@ -206,11 +212,8 @@ void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
 
 template <int MODE, int MAXP>
 void band_simt(cudaStream_t s, const BandTable<MAXP>& t) {
-  ktimer_begin(s, kKBandGemm);
-  band_pass_kernel<MODE, 0, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
-  ktimer_end(s);
-  ktimer_begin(s, kKBandExact);
-  band_pass_kernel<MODE, 1, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
+  ktimer_begin(s, kKBand);
+  band_pass_kernel<MODE, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
   ktimer_end(s);
 }
 
@@ -257,7 +260,7 @@ void half_step_band(fot_ctx* c, const float* pot_in, const float* lmarg, double 
   band_table_finish(t);
   band_prepare(c->stream, t);
   band_simt<kBandPot>(c->stream, t);
-  c->launches += 6;
+  c->launches += 4;
 }
 
 }  // namespace fot

@@ -43,8 +43,8 @@ __device__ __forceinline__ int chunk_dist(int j, int a, int b, int len) {
   return b < lo ? lo - b : (a > hi ? a - hi : 0);
 }
 
-// PATH 0 handles the items that take the tilted GEMM, PATH 1 the exact-window items; the two
-// variants are launched back to back and each skips the other's items (lean registers).
+// PATH 0 handles the items that take the tilted GEMM, PATH 1 the exact-window items; callers
+// invoke both and each returns at once on the other's items (the choice is warp-uniform).
 constexpr int kSA = 8 * 36 + 4;   // floats per half-warp A block (8 rows x 36, +4: banks)
 
 // The work of one (16-row group from row r0, 16-output tile) item; PATH 0 = tilted GEMM,

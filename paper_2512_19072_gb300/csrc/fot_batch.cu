@@ -1,8 +1,8 @@
 // Batched solve: many independent beam-shaping problems of different grid sizes in one
 // stream of multi-problem launches.
 //
-// Every axis pass of every problem goes into the same three launches (window plan and the two
-// banded window-sum kernels; window plan and the tensor-core kernel for the mixed form):
+// Every axis pass of every problem goes into the same two launches (the window plan, then the
+// banded window sums on the CUDA cores or, for the mixed form, on the tensor cores):
 // the kernels take a table of up to 64 problems by value and map each warp / CTA to its
 // problem by prefix sums (BandTable).  The whole solve - problem setup and all iterations
 // with each iteration's eps baked into its launches - is captured once into a CUDA graph and
@@ -83,14 +83,14 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         k += tc_pass<0>(st, *t1);
       } else {
         band_simt<0>(st, *t1);
-        k += 2;
+        k += 1;
       }
       band_prepare(st, *t2);
       if (use_tc) {
         k += tc_pass<1>(st, *t2);
       } else {
         band_simt<1>(st, *t2);
-        k += 2;
+        k += 1;
       }
       k += 2;                                             // the two plan launches
     }

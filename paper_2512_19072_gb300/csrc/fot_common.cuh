@@ -33,11 +33,10 @@ __device__ __forceinline__ bool error_latched(const int* err) {
 // context with timing on runs its loop, g_ktimer points at its timer and every launch site
 // brackets its kernel with a pair of events; fot_kernel_times sums them per class.
 enum KernelClass : int {
-  kKPlan = FOT_KERNEL_PLAN,             // band_plan_kernel
-  kKBandGemm = FOT_KERNEL_BAND_GEMM,    // band_pass_kernel, tilted-GEMM items
-  kKBandExact = FOT_KERNEL_BAND_EXACT,  // band_pass_kernel, exact-window items
-  kKTensor = FOT_KERNEL_TENSOR,         // tc_pass_kernel
-  kKDense = FOT_KERNEL_DENSE,           // axis_pass_kernel (dense exact pass)
+  kKPlan = FOT_KERNEL_PLAN,       // band_plan_kernel
+  kKBand = FOT_KERNEL_BAND,       // band_pass_kernel
+  kKTensor = FOT_KERNEL_TENSOR,   // tc_pass_kernel
+  kKDense = FOT_KERNEL_DENSE,     // axis_pass_kernel (dense exact pass)
   kKClasses = FOT_KERNEL_CLASSES
 };
 

@@ -422,7 +422,7 @@ template <int MODE, int MAXP>
 int tc_pass(cudaStream_t s, const BandTable<MAXP>& t) {
   if (!tc_useful(t)) {
     band_simt<MODE>(s, t);
-    return 2;
+    return 1;
   }
   ktimer_begin(s, kKTensor);
   tc_pass_kernel<MODE, MAXP><<<t.ctas, kThreads, kSmemBytes, s>>>(t);
@@ -449,7 +449,7 @@ void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double ep
   t.p[0].tc_terms = ts->tc_terms;
   band_table_finish(t);
   band_prepare(c->stream, t);
-  int k = 2 + tc_pass<0>(c->stream, t);
+  int k = 2 + tc_pass<0>(c->stream, t);   // + the two plan launches
   t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
   t.p[0].y = pot_out;
   t.p[0].lmarg = lmarg;

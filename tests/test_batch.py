@@ -42,15 +42,9 @@ def test_batch_equals_single_solves(fot_lib, prec):
     Gs = [to_dev(G) for _, G in probs]
     B.fot_batch_solve(batch, gs, Gs, eps, iters)
     kernels, tensor = B.fot_batch_info(batch)
-    # per axis pass: the window plan, then the two CUDA-core kernels (FP32), or the tensor
-    # kernel when some problem's eps allows a tensor-core tile (8 x 64 x c <= 40,
-    # c = log2(e) / (2 eps), in FP32 like the host check) and the CUDA-core kernels otherwise
-    per_pass = []
-    for t in range(iters):
-        c = np.float32(1.4426950408889634 / (2.0 * eps[:, t]))
-        tc = prec == "mixed" and bool((np.float32(8.0) * np.float32(64.0) * c <= np.float32(40.0)).any())
-        per_pass.append(1 + (1 if tc else 2))
-    assert kernels == 3 * len(probs) + 4 * sum(per_pass)
+    # problem setup (3 kernels each), then per axis pass the window plan and one window-sum
+    # kernel (CUDA cores, or tensor cores when some problem's eps allows a tensor tile)
+    assert kernels == 3 * len(probs) + iters * 4 * 2
     assert tensor == (prec == "mixed")
     for q, (g, G) in enumerate(probs):
         f, psi = B.fot_potentials(B.fot_batch_context(batch, q))

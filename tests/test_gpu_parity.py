@@ -381,8 +381,9 @@ def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
     assert err <= POT_RTOL * np.abs(f_ref[fin]).max() + mixed_atol(eps), (err, mixed_atol(eps))
     if eps >= 3000.0:
         assert tensor_terms > 0          # these tiles satisfy the tilt bounds: tensor cores used
-    if eps <= 12.0:
-        assert split[0] + split[1] > 0, split   # CUDA-core window sums ran
+    if eps == 4.0 or (eps == 12.0 and n > 64):
+        assert split[0] + split[1] > 0, split   # CUDA-core window sums ran (at 64^2 and eps 12
+                                                # every tile meets the tensor kernel's bound)
     if eps == 4.0:
         assert split[2] == 0, split            # no tile can meet the tilt bound at eps 4
     ctx.close()
