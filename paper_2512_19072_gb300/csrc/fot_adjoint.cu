@@ -68,16 +68,13 @@ __global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ x, 
     y[i] += s * x[i];
 }
 
-// moments VJP, elementwise part: zx = Dxbar e^{-S}, zy = Dybar e^{-S};
-// fbar += (Dxbar Dx + Dybar Dy)/eps; abar -= (Dxbar Dx + Dybar Dy)
+// moments VJP, elementwise part: fbar += (Dxbar Dx + Dybar Dy)/eps; abar -= (Dxbar Dx +
+// Dybar Dy).  (The kernel applications to Dxbar e^{-S}, Dybar e^{-S} take S as the log
+// offset of split_kernel: e^{-S} alone overflows FP32 where S is very negative.)
 __global__ void moments_vjp_pre(const float* __restrict__ Dxb, const float* __restrict__ Dyb,
-                                const float* __restrict__ Dx, const float* __restrict__ Dy,
-                                const float* __restrict__ S, float inv_eps, size_t N, float* __restrict__ zx,
-                                float* __restrict__ zy, float* __restrict__ fbar, float* __restrict__ abar) {
+                                const float* __restrict__ Dx, const float* __restrict__ Dy, float inv_eps,
+                                size_t N, float* __restrict__ fbar, float* __restrict__ abar) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
-    const float w = S[i] == -INFINITY ? 0.f : expf(-S[i]);
-    zx[i] = Dxb[i] * w;
-    zy[i] = Dyb[i] * w;
     const float d = Dxb[i] * Dx[i] + Dyb[i] * Dy[i];
     fbar[i] += d * inv_eps;
     abar[i] -= d;
@@ -225,8 +222,6 @@ extern "C" fot_status fot_backward(fot_ctx* c, const float* g, const float* G, c
   float* tB = alloc(N);
   float* Lp = alloc(N);
   float* Ln = alloc(N);
-  float* L2p = alloc(N);
-  float* L2n = alloc(N);
   float* scratch = alloc(N);
   float* psi_cur = alloc(N);
   float* f_cur = alloc(N);
@@ -274,14 +269,12 @@ extern "C" fot_status fot_backward(fot_ctx* c, const float* g, const float* G, c
     float* Dx = Lp;
     float* Dy = Ln;
     moments_simt(c, psi_cur, c->S_last, eT, c->dx, Dx, Dy);
-    float* zx = L2p;
-    float* zy = L2n;
-    moments_vjp_pre<<<gN, 256, 0, s>>>(Dxb, Dyb, Dx, Dy, c->S_last, (float)(1.0 / eT), N, zx, zy, fb, ab);
-    // K(zx), K(zy) on the target grid (4 log-domain applications)
-    split_kernel<<<gN, 256, 0, s>>>(zx, nullptr, (float)eT, N, pp, pn);
+    moments_vjp_pre<<<gN, 256, 0, s>>>(Dxb, Dyb, Dx, Dy, (float)(1.0 / eT), N, fb, ab);
+    // K(Dxbar e^{-S}), K(Dybar e^{-S}) on the target grid (4 log-domain applications)
+    split_kernel<<<gN, 256, 0, s>>>(Dxb, c->S_last, (float)eT, N, pp, pn);
     half_step_dispatch(c, pp, neg_inf, eT, scratch, lxp);
     half_step_dispatch(c, pn, neg_inf, eT, scratch, lxn);
-    split_kernel<<<gN, 256, 0, s>>>(zy, nullptr, (float)eT, N, pp, pn);
+    split_kernel<<<gN, 256, 0, s>>>(Dyb, c->S_last, (float)eT, N, pp, pn);
     half_step_dispatch(c, pp, neg_inf, eT, scratch, lyp);
     half_step_dispatch(c, pn, neg_inf, eT, scratch, lyn);
     moments_vjp_post<<<gN, 256, 0, s>>>(psi_cur, (float)(1.0 / eT), lxp, lxn, lyp, lyn, c->rows, c->cols,

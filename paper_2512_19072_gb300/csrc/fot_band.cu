@@ -35,8 +35,8 @@
 
 namespace fot {
 
-// Per (row, 16-output tile) plan: exact centre offset alpha, window start lo and length wl.
-// One CTA per row.  The row, scaled to log2 units, is staged in shared memory with one pad
+// Per (row, tile) plan (tiles of tile_w = 16 or 64 outputs): exact centre offset alpha, window
+// start lo and length wl.  One CTA per row.  The row, scaled to log2 units, is staged in shared memory with one pad
 // word per 32-wide chunk (threads scanning different chunks at the same offset hit different
 // banks), together with the chunk maxima and the row maximum.  Each thread then plans its
 // own tiles:
@@ -85,8 +85,9 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
 
+  const int tw = a.tile_w;
   for (int t = tid; t < T; t += kPlanThreads) {
-    const int k0 = t * kBT, kc = k0 + kBT / 2, k1 = min(k0 + kBT, len) - 1;
+    const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
     float best = -INFINITY;
     int arg = 0;
     auto scan = [&](int j) {
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
 }
 
 #ifndef FOT_BAND_MIN_BLOCKS
-#define FOT_BAND_MIN_BLOCKS 3   // resident CTAs per SM the register budget is sized for
+#define FOT_BAND_MIN_BLOCKS 2   // resident CTAs per SM the register budget is sized for (at 3
+                                // the 80-register budget spills; measured slower)
 #endif
 
 template <int MODE, int MAXP>
@@ -177,8 +179,8 @@ __global__ void __launch_bounds__(kBW * 32, FOT_BAND_MIN_BLOCKS) band_pass_kerne
   const int lw = gw - a.item_base;
   const int tile = lw % a.n_tiles, r0 = (lw / a.n_tiles) * 2 * kBR;
   // each item takes exactly one of the two (warp-uniform choice inside band_item)
-  band_item<MODE, 0>(a, r0, tile, sA[warp]);
-  band_item<MODE, 1>(a, r0, tile, sA[warp]);
+  band_item<MODE, 0>(a, r0, tile, tile * kBT, sA[warp]);
+  band_item<MODE, 1>(a, r0, tile, tile * kBT, sA[warp]);
 }
 
 template <int MAXP>
@@ -187,7 +189,7 @@ void band_table_finish(BandTable<MAXP>& t) {
   for (int q = 0; q < t.n; ++q) {
     BandArgs& a = t.p[q];
     a.n_chunks = (a.len + kCW - 1) / kCW;
-    a.n_tiles = (a.len + kBT - 1) / kBT;
+    a.n_tiles = (a.len + a.tile_w - 1) / a.tile_w;
     a.row_base = rows;
     a.plan_base = plans;
     a.item_base = items;
@@ -238,6 +240,7 @@ BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, 
   a.eps = (float)eps;
   a.n_rows = n_rows;
   a.len = len;
+  a.tile_w = kBT;
   return a;
 }
 

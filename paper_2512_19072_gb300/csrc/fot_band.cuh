@@ -7,7 +7,7 @@
 namespace fot {
 
 // One problem's pass.  plan holds alpha (float), window start and window length (int) per
-// (row, 16-output tile), n_rows * n_tiles words each, consecutive.
+// (row, tile of tile_w outputs), n_rows * n_tiles words each, consecutive.
 struct BandArgs {
   const float* x;      // [n_rows][len] input
   float* plan;
@@ -19,6 +19,7 @@ struct BandArgs {
                                  // [0] tilted-GEMM items, [1] exact-window items
   unsigned long long* tc_terms;  // += triples evaluated on the tensor cores
   float x_scale, c, eps;
+  int tile_w;          // outputs per plan tile: 16 (CUDA-core and 16-wide tensor passes) or 64
   int n_rows, len, n_chunks, n_tiles;
   int row_base, plan_base, item_base, cta_base;   // first global work index of each kernel
 };
@@ -64,10 +65,11 @@ void band_prepare(cudaStream_t s, const BandTable<MAXP>& t);
 template <int MODE, int MAXP>
 void band_simt(cudaStream_t s, const BandTable<MAXP>& t);
 
-// the tensor-core window sums (fot_tc.cu); tiles outside its tilt bound take the CUDA-core
-// sums inside the same kernel, and a pass where no tile can meet the bound runs band_simt.
-// Returns the number of kernels launched.
+// a whole pass on the tensor cores (fot_tc.cu): picks the tile width from eps, finishes the
+// table, plans and launches; tiles outside the tilt bound take the CUDA-core sums inside the
+// same kernel, and a pass where no tile can meet the bound runs band_simt.  Returns the
+// number of kernels launched.
 template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, const BandTable<MAXP>& t);
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t);
 
 }  // namespace fot

@@ -47,11 +47,14 @@ __device__ __forceinline__ int chunk_dist(int j, int a, int b, int len) {
 // invoke both and each returns at once on the other's items (the choice is warp-uniform).
 constexpr int kSA = 8 * 36 + 4;   // floats per half-warp A block (8 rows x 36, +4: banks)
 
-// The work of one (16-row group from row r0, 16-output tile) item; PATH 0 = tilted GEMM,
+// The work of one (16-row group from row r0, 16 outputs from k0) item; PATH 0 = tilted GEMM,
 // PATH 1 = exact window sums.  Returns at once when the item belongs to the other PATH.
+// The plan entry is (row, pt): with a 16-wide plan pt = k0 / 16; a wider plan tile holding
+// these outputs gives a window that covers theirs, and then only PATH 1 may be used
+// (EXACT_ONLY), since its alpha is not the maximum at this item's centre.
 // sAw: this warp's 2 * kSA floats of shared memory.
-template <int MODE, int PATH>
-__device__ __forceinline__ void band_item(const BandArgs& a, int r0, int tile, float* sAw) {
+template <int MODE, int PATH, bool EXACT_ONLY = false>
+__device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int k0, float* sAw) {
   const int lane = threadIdx.x & 31;
   const int h = lane >> 4, i = lane & 15;
   const size_t np = (size_t)a.n_rows * a.n_tiles;
@@ -59,7 +62,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int tile, f
   const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
   const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
   const int rh = r0 + h * kBR;                             // this half's first row
-  const int k0 = tile * kBT, kc = k0 + kBT / 2;
+  const int kc = k0 + kBT / 2;
   const int k1 = min(k0 + kBT, a.len) - 1;
   const float c = a.c, sc = a.x_scale;
 
@@ -70,7 +73,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int tile, f
   for (int rr = 0; rr < kBR; ++rr) {
     const int r = rh + rr;
     if (r < a.n_rows) {
-      const size_t pi = (size_t)r * a.n_tiles + tile;
+      const size_t pi = (size_t)r * a.n_tiles + pt;
       alpha[rr] = p_alpha[pi];
       lo[rr] = p_lo[pi];
       wl[rr] = p_wl[pi];
@@ -89,7 +92,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int tile, f
 #pragma unroll
   for (int rr = 0; rr < kBR; ++rr) out[rr] = -INFINITY;
 
-  const bool gemm = W > 0 && kmax * (float)W * c <= kTiltMax && kmax * kmax * c <= 32.f;
+  const bool gemm = !EXACT_ONLY && W > 0 && kmax * (float)W * c <= kTiltMax && kmax * kmax * c <= 32.f;
   if (gemm != (PATH == 0)) return;                        // the other variant's item
   if (i == 0) {                                           // lanes 0 and 16: per-half count
     unsigned long long t = 0;

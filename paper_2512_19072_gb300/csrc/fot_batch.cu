@@ -76,23 +76,18 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         t1->p[q] = a1;
         t2->p[q] = a2;
       }
-      band_table_finish(*t1);
-      band_table_finish(*t2);
-      band_prepare(st, *t1);
       if (use_tc) {
         k += tc_pass<0>(st, *t1);
-      } else {
-        band_simt<0>(st, *t1);
-        k += 1;
-      }
-      band_prepare(st, *t2);
-      if (use_tc) {
         k += tc_pass<1>(st, *t2);
       } else {
+        band_table_finish(*t1);
+        band_prepare(st, *t1);
+        band_simt<0>(st, *t1);
+        band_table_finish(*t2);
+        band_prepare(st, *t2);
         band_simt<1>(st, *t2);
-        k += 1;
+        k += 4;
       }
-      k += 2;                                             // the two plan launches
     }
   }
   delete t1;

@@ -6,8 +6,10 @@
 //     B[m'][kap] = 2^(2 kap (m' - W/2) c - kap^2 c)                     (same for all rows)
 // after which y[kc + kap][r] = alpha_r + 2 kap (lo_r + W/2 - kc) c + log2 C[r][kap] (the
 // per-row max-offsets of Sec. 3.1's Toeplitz contraction, plus the tilt).  One CTA computes
-// a 128-row x 16-output tile with tcgen05.mma (M = 128, N = 16, K = 16 per instruction), the
-// FP32 accumulator in tensor memory.  The operands are generated in shared memory by all
+// a 128-row x TN-output tile (TN = 16 or 64) with tcgen05.mma (M = 128, N = TN, K = 16 per
+// instruction), the FP32 accumulator in tensor memory.  A 64-wide tile needs one A operand
+// (one exponential per row and window position) for four times the outputs of a 16-wide
+// one; it is used when eps is large enough for the tilt bound at |kap| <= 32.  The operands are generated in shared memory by all
 // 256 threads (one exponential per element) in the canonical no-swizzle K-major layout,
 // double-buffered against the MMAs through mbarriers that tcgen05.commit arrives on.
 //
@@ -15,9 +17,12 @@
 // lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
 // about 2^-16 relative per product instead of 2^-8, FP32 accumulation.
 //
-// A CTA uses the tensor cores only when the tilt bounds of the banded pass hold for the
-// common window length W of its 128 rows; otherwise its eight warps compute the tile with
-// the CUDA-core window sums of the banded pass (16 rows each).  Every mbarrier wait is
+// A CTA uses the tensor cores only when the tilt bound holds for the common window length W
+// of its 128 rows: |kap| W c <= 48 with |kap| <= TN / 2.  Then every output's largest term has
+// A >= 2^-96, and the A values that flush below 2^-126 add less than W 2^-30 relative: below
+// the 2^-16 of the split-BF16 products.  Otherwise its eight warps compute the tile with the
+// CUDA-core window sums of the banded pass (16 rows each; for a 64-wide tile the exact window
+// sums over the tile's window, which covers the windows of its 16-wide parts).  Every mbarrier wait is
 // bounded: on time-out the kernel latches FOT_ETIMEOUT, stops issuing, frees its tensor
 // memory and returns.
 #include "fot_band_item.cuh"
@@ -31,19 +36,20 @@ namespace fot {
 namespace {
 
 constexpr int kTM = 128;            // rows per CTA (MMA M, TMEM lanes)
-constexpr int kTN = 16;             // outputs per CTA (MMA N)
 constexpr int kKC = 64;             // window positions per pipeline stage
 constexpr int kThreads = 256;
-constexpr float kTiltMaxTC = 40.f;
-constexpr uint32_t kTmemCols = 32;  // FP32 accumulator columns (minimum allocation; kTN used)
+constexpr float kTiltMaxTC = 48.f;
 constexpr int kSpin = 1 << 20;      // bounded mbarrier polls
 
 // shared-memory layout of one stage (bytes): A_hi, A_lo (128 x 64 bf16 each), B_hi, B_lo
-// (16 x 64 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 1024 + kg * 128.
+// (TN x 64 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 1024 + kg * 128.
 constexpr int kABytes = kTM * kKC * 2;   // 16384
-constexpr int kBBytes = kTN * kKC * 2;   // 2048
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-constexpr int kSmemBytes = 2 * kStageBytes + 1024;   // 2 stages + barriers/params + slack
+template <int TN> struct TcShape {
+  static constexpr int kBBytes = TN * kKC * 2;
+  static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+  static constexpr int kSmemBytes = 2 * kStageBytes + 1024;   // 2 stages + slack
+  static constexpr uint32_t kTmemCols = TN < 32 ? 32 : TN;    // power of two >= 32
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -122,8 +128,12 @@ __device__ __forceinline__ void store_split8(const float* v, uint32_t hi_addr, u
                "r"(pack_bf16(l[6], l[7])) : "memory");
 }
 
-template <int MODE, int MAXP>
+template <int MODE, int TN, int MAXP>
 __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+  constexpr int kTN = TN;
+  constexpr int kStageBytes = TcShape<TN>::kStageBytes;
+  constexpr int kBBytes = TcShape<TN>::kBBytes;
+  constexpr uint32_t kTmemCols = TcShape<TN>::kTmemCols;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base_sh;
@@ -170,8 +180,13 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
     const int rw = r0 + warp * 2 * kBR;                 // this warp's 16 rows
     if (rw < a.n_rows) {
       float* sAw = reinterpret_cast<float*>(smem) + warp * 2 * kSA;
-      band_item<MODE, 0>(a, rw, tile, sAw);
-      band_item<MODE, 1>(a, rw, tile, sAw);
+      if (TN == kBT) {
+        band_item<MODE, 0>(a, rw, tile, k0, sAw);
+        band_item<MODE, 1>(a, rw, tile, k0, sAw);
+      } else {
+        for (int q = 0; q < TN / kBT && k0 + q * kBT < a.len; ++q)
+          band_item<MODE, 1, true>(a, rw, tile, k0 + q * kBT, sAw);
+      }
     }
     return;
   }
@@ -198,14 +213,11 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   bool ok = true;
 
   // producer roles: A row r = tid % 128, half h = tid / 128 (32 window positions each);
-  // B (threads 0..127): output n = tid % 16, positions (tid / 16) * 8 .. + 8
+  // B: core rows q = tid, tid + 256, ... of TN outputs x 8 groups of 8 positions
   const int ar = tid & (kTM - 1), ah = tid >> 7;
   const float a_alpha = s_alpha[ar];
   const int a_lo = s_lo[ar];
   const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
-  const int bn = tid & (kTN - 1), bq = (tid >> 4) & 7;
-  const float bkap = (float)(bn - kTN / 2);
-  const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
 
   const int nchunk = W / kKC;
   // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
@@ -266,8 +278,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
       const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
       store_split8(v, sAhi + off, sAlo + off);
     }
-    // B: 8 window positions of output bn
-    if (tid < kTN * 8) {
+    // B: 8 window positions of output bn per core row
+#pragma unroll
+    for (int q = tid; q < kTN * (kKC / 8); q += kThreads) {
+      const int bn = q % kTN, bq = q / kTN;
+      const float bkap = (float)(bn - kTN / 2);
+      const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
       float v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -306,51 +322,56 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   ok = __syncthreads_and(ok && ok_end);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  if (ok && warp < 4) {
-    // accumulator row = TMEM lane = 32 * warp + lane, columns = the 16 outputs
-    uint32_t acc[kTN];
-    const uint32_t taddr = tmem_d + ((uint32_t)(32 * warp) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15}, [%16];"
-        : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
-          "=r"(acc[6]), "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]),
-          "=r"(acc[12]), "=r"(acc[13]), "=r"(acc[14]), "=r"(acc[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int rloc = 32 * warp + lane;
+  if (ok) {
+    // accumulator row = TMEM lane = 32 * (warp % 4) + lane; warps w and w + 4 take the two
+    // halves of the TN columns, 8 at a time
+    const int lq = warp & 3, ch = warp >> 2;
+    const int rloc = 32 * lq + lane;
     const int r = r0 + rloc;
     const float al = s_alpha[rloc];
     const float mref = (float)s_lo[rloc] + halfW;
-    if (r < a.n_rows) {
 #pragma unroll
-      for (int n = 0; n < kTN; ++n) {
-        const int k = k0 + n;
-        if (k > k1) break;
-        const float kap = (float)(n - kTN / 2);
-        const float cv = __uint_as_float(acc[n]);
-        float out = -INFINITY;
-        if (al != -INFINITY) {
-          if (cv > 0.f && isfinite(cv))
-            out = al + 2.f * kap * (mref - (float)kc) * c + log2f(cv);
-          else
-            raise_error(a.err, FOT_ENONFINITE);
-        }
-        const size_t yi = (size_t)k * a.n_rows + r;
-        if (MODE == 0) {
-          a.y[yi] = out;
-        } else {
-          const float sv = out * kLn2;
-          const float lm = a.lmarg[yi];
-          float pot;
-          if (lm == -INFINITY) {
-            pot = -INFINITY;
-          } else {
-            pot = a.eps * (lm - sv);
-            if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
+    for (int cg = 0; cg < kTN / 2; cg += 8) {
+      const int n0 = ch * (kTN / 2) + cg;
+      uint32_t acc[8];
+      const uint32_t taddr = tmem_d + ((uint32_t)(32 * lq) << 16) + (uint32_t)n0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
+            "=r"(acc[6]), "=r"(acc[7])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (r < a.n_rows) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int n = n0 + u;
+          const int k = k0 + n;
+          if (k > k1) break;
+          const float kap = (float)(n - kTN / 2);
+          const float cv = __uint_as_float(acc[u]);
+          float out = -INFINITY;
+          if (al != -INFINITY) {
+            if (cv > 0.f && isfinite(cv))
+              out = al + 2.f * kap * (mref - (float)kc) * c + log2f(cv);
+            else
+              raise_error(a.err, FOT_ENONFINITE);
           }
-          a.y[yi] = pot;
-          if (a.logsum) a.logsum[yi] = sv;
+          const size_t yi = (size_t)k * a.n_rows + r;
+          if (MODE == 0) {
+            a.y[yi] = out;
+          } else {
+            const float sv = out * kLn2;
+            const float lm = a.lmarg[yi];
+            float pot;
+            if (lm == -INFINITY) {
+              pot = -INFINITY;
+            } else {
+              pot = a.eps * (lm - sv);
+              if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
+            }
+            a.y[yi] = pot;
+            if (a.logsum) a.logsum[yi] = sv;
+          }
         }
       }
     }
@@ -380,10 +401,16 @@ int tc_create(fot_ctx* c) {
     return 1;
   }
   // dynamic shared memory above 48 KB, for every instance (before any stream capture)
-  if (cudaFuncSetAttribute(tc_pass_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(tc_pass_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(tc_pass_kernel<0, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(tc_pass_kernel<1, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
+  bool ok = true;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 64, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
+  if (!ok) {
     cudaFree(t->tc_terms);
     delete t;
     return 1;
@@ -409,32 +436,47 @@ int64_t tc_terms(fot_ctx* c) {
   return (int64_t)v;
 }
 
-// true when some problem of the table can meet the tilt bound: a taken tile has W >= kKC,
-// so c > kTiltMaxTC / (kTN / 2 * kKC) rules the tensor cores out for the whole pass
+// Tile width of a tensor-core pass from the largest c of the table's problems:
+//  64 when a 64-wide tile is expected to meet the tilt bound: its window spans the tile plus
+//     about sqrt(kCut / c) on each side (where the Gaussian kernel alone falls by 2^-kCut),
+//     rounded up to whole stages, and |kap| W c <= kTiltMaxTC at |kap| = 32;
+//  16 when a 16-wide tile can meet it at all (a taken tile has W >= kKC);
+//   0 when neither: the pass runs the CUDA-core kernels.
 template <int MAXP>
-bool tc_useful(const BandTable<MAXP>& t) {
-  for (int q = 0; q < t.n; ++q)
-    if ((float)(kTN / 2) * (float)kKC * t.p[q].c <= kTiltMaxTC) return true;
-  return false;
+int tc_width(const BandTable<MAXP>& t) {
+  float cmax = 0.f;
+  for (int q = 0; q < t.n; ++q) cmax = fmaxf(cmax, t.p[q].c);
+  const float w64 = 64.f + 2.f * sqrtf(kCut / cmax);
+  const float w64r = ceilf(w64 / (float)kKC) * (float)kKC;
+  if (32.f * w64r * cmax <= kTiltMaxTC && 32.f * 32.f * cmax <= 32.f) return 64;
+  if ((float)(kBT / 2) * (float)kKC * cmax <= kTiltMaxTC) return 16;
+  return 0;
 }
 
 template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, const BandTable<MAXP>& t) {
-  if (!tc_useful(t)) {
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t) {
+  const int tw = tc_width(t);
+  for (int q = 0; q < t.n; ++q) t.p[q].tile_w = tw == 64 ? 64 : kBT;
+  band_table_finish(t);
+  band_prepare(s, t);
+  if (tw == 0) {
     band_simt<MODE>(s, t);
-    return 1;
+    return 2;
   }
   ktimer_begin(s, kKTensor);
-  tc_pass_kernel<MODE, MAXP><<<t.ctas, kThreads, kSmemBytes, s>>>(t);
+  if (tw == 64)
+    tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreads, TcShape<64>::kSmemBytes, s>>>(t);
+  else
+    tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreads, TcShape<16>::kSmemBytes, s>>>(t);
   ktimer_end(s);
-  return 1;
+  return 2;
 }
 
 unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
-template int tc_pass<0, 1>(cudaStream_t, const BandTable<1>&);
-template int tc_pass<1, 1>(cudaStream_t, const BandTable<1>&);
-template int tc_pass<0, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
-template int tc_pass<1, kMaxBatch>(cudaStream_t, const BandTable<kMaxBatch>&);
+template int tc_pass<0, 1>(cudaStream_t, BandTable<1>&);
+template int tc_pass<1, 1>(cudaStream_t, BandTable<1>&);
+template int tc_pass<0, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&);
+template int tc_pass<1, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&);
 
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 
@@ -447,16 +489,12 @@ void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double ep
   t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
   t.p[0].y = c->R;
   t.p[0].tc_terms = ts->tc_terms;
-  band_table_finish(t);
-  band_prepare(c->stream, t);
-  int k = 2 + tc_pass<0>(c->stream, t);   // + the two plan launches
+  int k = tc_pass<0>(c->stream, t);
   t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
   t.p[0].y = pot_out;
   t.p[0].lmarg = lmarg;
   t.p[0].logsum = logsum;
   t.p[0].tc_terms = ts->tc_terms;
-  band_table_finish(t);
-  band_prepare(c->stream, t);
   k += tc_pass<1>(c->stream, t);
   c->launches += k;
 }

@@ -93,37 +93,57 @@ def test_autograd_function_and_checkpoint_invariance(fot_lib):
 
 
 def test_adjoint_backward_workload_directional_fd(fot_lib):
-    """512^2, 100 iterations at eps = 4 px^2, checkpoint every 10: the adjoint gradient agrees
-    with central differences of the GPU forward along seeded smooth directions."""
+    """512^2, 100 iterations at eps = 4 px^2, checkpoint every 10: the adjoint gradients of a
+    phase loss and of a potentials loss agree with central differences of the GPU forward
+    along seeded smooth directions.  (At this eps the 100 iterations are far from converged and
+    the moment weights' row sums are far from 1, so the phase loss is large; its central
+    differences are stable from h = 1e-2 down to 1e-4.)"""
     B = fot_lib
     w4 = inputs.config4()
     n = 512
     g, G = f32(w4.g), f32(w4.G)
     wt, phit = to_dev(f32(w4.extra["w"])), to_dev(f32(w4.extra["phi_target"]))
+    w2 = to_dev(f32(np.random.default_rng(45).uniform(0, 1, size=(n, n))))
     ctx = B.fot_create(n, n)
     gt, Gt = to_dev(g), to_dev(G)
 
-    def loss(gg, GG):
+    def run(gg, GG):
         B.fot_solve(ctx, gg, GG, w4.eps, w4.iters)
         phi, _, _ = B.fot_phase(ctx)
-        return (wt.double() * phi.double()).sum().item() + ((phi.double() - phit.double()) ** 2).sum().item(), phi
+        f, psi = B.fot_potentials(ctx)
+        return phi.double(), f.double(), psi.double()
 
-    L0, phi = loss(gt, Gt)
-    dg, dG = B.fot_backward(ctx, gt, Gt, dL_dphi=_loss_seed(phi, wt, phit), checkpoint_every=10)
+    def losses(r):
+        phi, f, psi = r
+        fin_f = torch.where(torch.isfinite(f), f, torch.zeros_like(f))
+        fin_p = torch.where(torch.isfinite(psi), psi, torch.zeros_like(psi))
+        Lph = (wt.double() * phi).sum().item() + ((phi - phit.double()) ** 2).sum().item()
+        Lpo = (w2.double() * fin_p).sum().item() + (wt.double() * fin_f).sum().item()
+        return Lph, Lpo
+
+    phi, f, psi = run(gt, Gt)
+    grads = {}
+    grads["phase"] = B.fot_backward(ctx, gt, Gt, dL_dphi=_loss_seed(phi.float(), wt, phit),
+                                    checkpoint_every=10)
+    dL_df = torch.where(torch.isfinite(f), wt.double(), torch.zeros_like(f)).float().contiguous()
+    dL_dpsi = torch.where(torch.isfinite(psi), w2.double(), torch.zeros_like(psi)).float().contiguous()
+    grads["pot"] = B.fot_backward(ctx, gt, Gt, dL_df=dL_df, dL_dpsi=dL_dpsi, checkpoint_every=10)
+    for dg, dG in grads.values():
+        assert torch.isfinite(dg).all() and torch.isfinite(dG).all()
     rng = np.random.default_rng(44)
     x = np.linspace(-1, 1, n)
+    h = 1e-2
     for which in ("g", "G"):
         base = g if which == "g" else G
-        grad = (dg if which == "g" else dG).double().cpu().numpy()
         for _ in range(2):
             a = rng.normal(size=3)
             v = base * (a[0] + a[1] * x[:, None] + a[2] * x[None, :])      # smooth relative direction
-            h = 1e-2
-            p = to_dev(base + h * v)
-            m = to_dev(base - h * v)
-            Lp = loss(p, Gt)[0] if which == "g" else loss(gt, p)[0]
-            Lm = loss(m, Gt)[0] if which == "g" else loss(gt, m)[0]
-            fd = (Lp - Lm) / (2 * h)
-            ad = float((grad * v).sum())
-            assert abs(fd - ad) <= 2e-2 * abs(ad) + 1e-6 * abs(L0), (which, fd, ad)
+            p, m = to_dev(base + h * v), to_dev(base - h * v)
+            Lp = losses(run(p, Gt) if which == "g" else run(gt, p))
+            Lm = losses(run(m, Gt) if which == "g" else run(gt, m))
+            for k, kind in enumerate(("phase", "pot")):
+                grad = grads[kind][0 if which == "g" else 1].double().cpu().numpy()
+                fd = (Lp[k] - Lm[k]) / (2 * h)
+                ad = float((grad * v).sum())
+                assert abs(fd - ad) <= 2e-2 * abs(ad), (which, kind, fd, ad)
     ctx.close()

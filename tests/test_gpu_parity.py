@@ -356,11 +356,13 @@ def mixed_atol(eps):
 
 
 @pytest.mark.parametrize("shape", [(64, 64), (100, 130), (257, 200), (300, 300)])
-@pytest.mark.parametrize("eps", [4.0, 12.0, 60.0, 3000.0])
+@pytest.mark.parametrize("eps", [4.0, 12.0, 60.0, 300.0, 3000.0])
 def test_mixed_half_steps_match_oracle(fot_lib, shape, eps):
     """eps 4: no tile can meet the tensor kernel's tilt bound (the pass runs the CUDA-core
-    kernels); eps 12: the tensor kernel computes the tiles it declines with the CUDA-core
-    window sums inside the same launch; eps 60, 3000: mostly tensor-core tiles."""
+    kernels); eps 12: 16-wide tensor tiles, and the tiles the kernel declines are computed
+    with the CUDA-core window sums inside the same launch; eps 60: 16-wide tensor tiles;
+    eps 300: 64-wide tensor tiles, the noisy potential's long windows declining some of them
+    (exact window sums over the 64-wide tile's window); eps 3000: 64-wide tensor tiles."""
     B = fot_lib
     rng = np.random.default_rng(hash((shape, eps, "mixed")) % 2**32)
     g, G = _masses(rng, shape, 0.15)
