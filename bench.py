@@ -37,7 +37,9 @@ def _args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fot", choices=["fot", "reference"])
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp32_dense", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp32", "fp32_dense", "mixed"])
+    p.add_argument("--no-compare", action="store_true",
+                   help="skip the FP32 comparison run of the mixed form")
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -331,7 +333,35 @@ def run_gpu(a):
         cpu = None
         if not a.no_cpu_baseline and ws == 1:
             cpu = _oracle_sample(w, rows=32, budget_s=12.0)
-        line = {"metric": METRIC, "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
+        # the plain FP32 form on the same workload and steps (the metric compares the two)
+        compare = None
+        if a.precision == "mixed" and not a.no_compare:
+            c32 = B.fot_create(n, n, B.FOT_FP32)
+
+            def step32():
+                B.fot_solve(c32, g, G, eps, a.iters)
+                B._check(B._lib.fot_phase(c32._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
+
+            for _ in range(a.warmup):
+                flush.zero_()
+                step32()
+            ms32 = []
+            for _ in range(a.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step32()
+                e1.record(stream)
+                e1.synchronize()
+                ms32.append(e0.elapsed_time(e1))
+            l1_32, _ = B.fot_marginal_error(c32)
+            v32 = n * n * a.iters / (statistics.mean(ms32) * 1e-3) / 1e6
+            compare = {"precision": "fp32", "value": v32, "ms_per_step": statistics.mean(ms32),
+                       "marginal_l1": l1_32, "marginal_l1_diff": abs(l1 - l1_32),
+                       "mixed_speedup": value / v32}
+            c32.close()
+        line = {"metric": METRIC if n == 1024 else METRIC.replace("1024^2", f"{n}^2"), "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16+f32" if a.precision == "mixed" else "f32",
@@ -346,7 +376,7 @@ def run_gpu(a):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": "Mpixel*iter/s",
                         "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4},
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "fp32_form": compare,
                 "paper_context": "1024^2, 200 iterations: 76 s Core i7 (2.76 Mpixel*iter/s), "
                                  "8.5 s T4 (24.7 Mpixel*iter/s)"}
         print(json.dumps(line), flush=True)

@@ -8,10 +8,10 @@
 // band_plan_kernel (one CTA per row) and leave (alpha, lo, window length) per (row, tile);
 // steps 3-4 run in band_pass_kernel.
 //
-// 1. Exact offset at every tile centre kc = k0 + 8:  alpha_r = max_m e_r(m, kc),
-//    e_r(m, o) = x_r[m] - (o - m)^2 c, and its argmax, found by scanning only the 32-wide
-//    chunks of m whose upper bound (chunk maximum of x, nearest distance) beats the best
-//    term found so far.
+// 1. Offset at every tile centre kc = k0 + 8: a term alpha_r = e_r(m_r, kc) within 16 (log2
+//    units) of max_m e_r(m, kc), e_r(m, o) = x_r[m] - (o - m)^2 c, found by scanning only the
+//    32-wide chunks of m whose upper bound (chunk maximum of x, nearest distance) exceeds the
+//    best term found so far by more than that.
 // 2. A provable window: every o in the tile has max_m e_r(m, o) >= LB_r, with LB_r the
 //    value of the centre's argmax term at the worse tile end.  A 32-wide chunk of m whose
 //    upper bound (chunk maximum of x, nearest distance) over the whole tile is below
@@ -21,7 +21,7 @@
 //      e_r(m, o) = [x_r[m] - (kc - m)^2 c - alpha_r] + [2 kap (m - Mref_r) c - kap^2 c]
 //                  + alpha_r + 2 kap (Mref_r - kc) c,
 //    so  sum_m 2^e = 2^(alpha_r + 2 kap (Mref_r - kc) c) * sum_m' A[r][m'] B[m'][kap]
-//    with A[r][m'] = 2^(e_r(lo_r + m', kc) - alpha_r) <= 1 (one exponential per row and
+//    with A[r][m'] = 2^(e_r(lo_r + m', kc) - alpha_r) <= 2^16 (one exponential per row and
 //    window position, shared by the tile's outputs) and B[m'][kap] = 2^(2 kap (m' - W/2) c -
 //    kap^2 c), the same for every row once each row's window is indexed from its own start
 //    lo_r (Mref_r = lo_r + W/2).  This is a GEMM over the window, done with FFMAs; the
@@ -35,131 +35,138 @@
 
 namespace fot {
 
-// Per (row, tile) plan (tiles of tile_w = 16 or 64 outputs): exact centre offset alpha, window
-// start lo and length wl.  One CTA per row.  The row, scaled to log2 units, is staged in shared memory with one pad
-// word per 32-wide chunk (threads scanning different chunks at the same offset hit different
-// banks), together with the chunk maxima and the row maximum.  Each thread then plans its
-// own tiles:
-//   a. alpha: scan the chunk holding the centre kc, then every chunk whose upper bound
-//      (chunk maximum less the nearest squared distance times c) beats the running best.
-//      The bound never undershoots the rounded terms it stands for (d*d is exact and the
-//      fused multiply-add rounds monotonically), so the maximum is exact for any input;
-//      chunks farther from kc than sqrt((row max - best) / c) cannot qualify and are not
-//      visited.  For the concave rows of converged potentials one or two chunks qualify.
-//   b. the window of step 2 above, from the same chunk maxima.
+// Per (row, tile) plan (tiles of tile_w = 16, 32 or 64 outputs): centre offset alpha, window
+// start lo and length wl.  One CTA of four warps per row.  The row is staged in shared memory
+// as z[m] = x[m] * scale - u^2 c (u = m mod 32, one pad word per 32-wide chunk), with the
+// maxima of x * scale over 32-wide chunks and over 8-wide sub-chunks.  Each warp then plans
+// tiles one at a time:
+//   a. alpha: with d0 = kc - 32 j, e(32 j + u, kc) = z[32 j + u] + 2 c d0 u - c d0^2.  Lane l
+//      takes element l of the chunk holding the centre kc, and every sub-chunk it owns whose
+//      upper bound (sub-chunk maximum less the nearest squared distance times c) exceeds that
+//      chunk's best term by more than kAlphaSlack; one warp argmax over the lanes' best terms
+//      gives alpha and its index.  Every sub-chunk left out is bounded by alpha + kAlphaSlack,
+//      so alpha is a term within kAlphaSlack of the maximum: it only scales the window sums'
+//      operands (A <= 2^kAlphaSlack instead of <= 1, far from overflow, and the largest term
+//      of every output keeps A >= 2^-2 kTiltMax), and the window bound below needs a term.
+//   b. the window of step 2 above: the first and the last 32-wide chunk whose bound over the
+//      tile reaches LB - kCut (one ballot per 32 chunks).
 constexpr int kPlanThreads = 128;
-constexpr int kMaxChunks = 4096 / kCW;        // longest axis 4096
-constexpr int kMaskWords = kMaxChunks / 32;
+constexpr int kSub = 8;                       // sub-chunk width
+constexpr float kAlphaSlack = 16.f;           // alpha may sit this far (log2) below the maximum
 
 template <int MAXP>
 __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
-  __shared__ float s_x[kMaxChunks * (kCW + 1)];
-  __shared__ float s_cm[kMaxChunks];
-  __shared__ float s_rowmax;
+  extern __shared__ float s_plan[];   // [n_chunks * 33] z, [n_chunks] chunk maxima, [4 n_chunks] sub
   const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, (int)blockIdx.x)];
   if (error_latched(a.err)) return;                       // CTA-uniform
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int row = (int)blockIdx.x - a.plan_base;
   const int T = a.n_tiles, len = a.len, nch = a.n_chunks;
+  const int nsub = nch * (kCW / kSub);
+  const int nwords = (nch + 31) / 32, nswords = (nsub + 31) / 32;
   const float c = a.c, sc = a.x_scale;
   const float* xr = a.x + (size_t)row * len;
-  for (int m = tid; m < nch * kCW; m += kPlanThreads)
-    s_x[(m >> 5) * (kCW + 1) + (m & 31)] = m < len ? xr[m] * sc : -INFINITY;
-  __syncthreads();
-  // max(x) * sc == max(x * sc): sc > 0 and rounding is monotone
-  for (int j = warp; j < nch; j += kPlanThreads / 32) {
-    const float v = warp_max(s_x[j * (kCW + 1) + lane]);
-    if (lane == 0) s_cm[j] = v;
+  float* s_z = s_plan;
+  float* s_cm = s_plan + nch * (kCW + 1);
+  float* s_c8 = s_cm + nch;
+  // stage: each warp takes whole chunks, four at a time (lane = position in the chunk; the
+  // four loads are issued together); max(x) * sc equals max(x * sc) since sc > 0 and rounding
+  // is monotone
+  const float uc = -(float)(lane * lane) * c;
+  for (int j0 = warp * 4; j0 < nch; j0 += nw * 4) {
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = (j0 + q) * kCW + lane;
+      v[q] = (j0 + q < nch && m < len) ? __fmul_rn(xr[m], sc) : -INFINITY;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (j0 + q >= nch) break;                           // warp-uniform
+      s_z[(j0 + q) * (kCW + 1) + lane] = __fadd_rn(v[q], uc);   // no contraction: the same
+                                                                  // rounding in every instance
+      float mx = v[q];
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+      if ((lane & (kSub - 1)) == 0) s_c8[(j0 + q) * (kCW / kSub) + lane / kSub] = mx;
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+      if (lane == 0) s_cm[j0 + q] = mx;
+    }
   }
   __syncthreads();
-  if (warp == 0) {
-    float v = -INFINITY;
-    for (int j = lane; j < nch; j += 32) v = fmaxf(v, s_cm[j]);
-    v = warp_max(v);
-    if (lane == 0) s_rowmax = v;
-  }
-  __syncthreads();
-  const float X = s_rowmax;
   const size_t np = (size_t)a.n_rows * T;
   float* p_alpha = a.plan;
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
-
   const int tw = a.tile_w;
-  for (int t = tid; t < T; t += kPlanThreads) {
+
+  for (int t = warp; t < T; t += nw) {
     const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
-    float best = -INFINITY;
-    int arg = 0;
-    auto scan = [&](int j) {
-      const float* xs = &s_x[j * (kCW + 1)];
-      const float d0 = (float)(kc - j * kCW);
-#pragma unroll 8
-      for (int u = 0; u < kCW; ++u) {
-        const float d = d0 - (float)u;
-        const float v = fmaf(-d * d, c, xs[u]);
-        if (v > best) {
-          best = v;
-          arg = j * kCW + u;
+    // a. element `lane` of the centre's chunk, then this lane's qualifying sub-chunks
+    const int jc = min(kc, len - 1) / kCW;
+    const float dc = (float)(kc - jc * kCW);
+    float best = fmaf((float)lane, 2.f * c * dc, s_z[jc * (kCW + 1) + lane]);
+    best = fmaf(-dc * dc, c, best);
+    int arg = jc * kCW + lane;
+    const float floor_ = warp_max(best) + kAlphaSlack;  // sub-chunks at or below: left out
+#pragma unroll 1
+    for (int w = 0; w < nswords; ++w) {
+      const int sj = 32 * w + lane;
+      const int m0 = sj * kSub, m1 = min(m0 + kSub, len) - 1;
+      const int d = m0 > kc ? m0 - kc : (m1 < kc ? kc - m1 : 0);
+      const float c8 = sj < nsub ? s_c8[sj] : -INFINITY;
+      if (sj / (kCW / kSub) != jc && fmaf(-(float)d * (float)d, c, c8) > floor_) {
+        const int j = sj / (kCW / kSub), u0 = m0 - j * kCW;
+        const float d0 = (float)(kc - j * kCW);
+        const float t2 = 2.f * c * d0;
+        const float* zs = &s_z[j * (kCW + 1) + u0];
+#pragma unroll
+        for (int v = 0; v < kSub; ++v) {
+          const float e = fmaf(-d0 * d0, c, fmaf((float)(u0 + v), t2, zs[v]));
+          if (e > best) {
+            best = e;
+            arg = m0 + v;
+          }
         }
       }
-    };
-    // a. exact centre maximum
-    const int jc = min(kc, len - 1) / kCW;
-    scan(jc);
-    int jlo = 0, jhi = nch - 1;
-    if (best != -INFINITY) {          // a chunk at distance dist needs X - dist^2 c > best
-      const float R = sqrtf((X - best) / c) * 1.01f + 2.f * kCW;
-      jlo = (int)fmaxf(0.f, floorf(((float)kc - R) / (float)kCW));
-      jhi = (int)fminf((float)(nch - 1), floorf(((float)kc + R) / (float)kCW));
     }
-    unsigned cand[kMaskWords];
-#pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) {
-      unsigned mk = 0;
-      const int ja = max(jlo, 32 * w), jb = min(jhi, 32 * w + 31);
-      for (int j = ja; j <= jb; ++j) {
-        const float d = (float)chunk_dist(j, kc, kc, len);
-        if (j != jc && fmaf(-d * d, c, s_cm[j]) > best) mk |= 1u << (j - 32 * w);
-      }
-      cand[w] = mk;
-    }
-#pragma unroll
-    for (int w = 0; w < kMaskWords; ++w) {
-      unsigned mk = cand[w];
-      while (mk) {
-        const int j = 32 * w + __ffs(mk) - 1;
-        mk &= mk - 1;
-        const float d = (float)chunk_dist(j, kc, kc, len);
-        if (fmaf(-d * d, c, s_cm[j]) > best) scan(j);   // best may have risen meanwhile
-      }
-    }
+    warp_argmax(best, arg);
     const size_t pi = (size_t)row * T + t;
     if (best == -INFINITY) {                              // no finite term: empty row
-      p_alpha[pi] = -INFINITY;
-      p_lo[pi] = 0;
-      p_wl[pi] = 0;
+      if (lane == 0) {
+        p_alpha[pi] = -INFINITY;
+        p_lo[pi] = 0;
+        p_wl[pi] = 0;
+      }
       continue;
     }
+    const float al = best;
     // b. window: lower bound over the tile from the argmax term at the worse tile end, then
     // the first and the last chunk whose bound over the tile reaches lb - kCut
     const float dM = (float)(arg - kc);
     const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
-    const float lb = best + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
-    const float R2 = sqrtf((X - (lb - kCut)) / c) * 1.01f + 2.f * kCW;
-    const int ja = (int)fmaxf(0.f, floorf(((float)k0 - R2) / (float)kCW));
-    const int jb = (int)fminf((float)(nch - 1), floorf(((float)k1 + R2) / (float)kCW));
-    int wlo = ja, whi = jb;
-    for (; wlo < jb; ++wlo) {
-      const float d = (float)chunk_dist(wlo, k0, k1, len);
-      if (fmaf(-d * d, c, s_cm[wlo]) >= lb - kCut) break;
+    const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
+    int wlo = -1, whi = -1;
+#pragma unroll 1
+    for (int w = 0; w < nwords; ++w) {
+      const int j = 32 * w + lane;
+      const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
+      const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
+      const float cmj = j < nch ? s_cm[j] : -INFINITY;
+      const bool in = fmaf(-(float)d * (float)d, c, cmj) >= lb - kCut;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (bal) {
+        if (wlo < 0) wlo = 32 * w + __ffs(bal) - 1;
+        whi = 32 * w + 31 - __clz(bal);
+      }
     }
-    for (; whi > wlo; --whi) {
-      const float d = (float)chunk_dist(whi, k0, k1, len);
-      if (fmaf(-d * d, c, s_cm[whi]) >= lb - kCut) break;
+    if (lane == 0) {
+      p_alpha[pi] = al;
+      p_lo[pi] = wlo * kCW;
+      p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
     }
-    p_alpha[pi] = best;
-    p_lo[pi] = wlo * kCW;
-    p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
   }
 }
 
@@ -207,8 +214,11 @@ void band_table_finish(BandTable<MAXP>& t) {
 
 template <int MAXP>
 void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
+  int max_chunks = 1;
+  for (int q = 0; q < t.n; ++q) max_chunks = std::max(max_chunks, t.p[q].n_chunks);
+  const size_t smem = (size_t)max_chunks * (kCW + 2 + kCW / kSub) * sizeof(float);
   ktimer_begin(s, kKPlan);
-  band_plan_kernel<MAXP><<<t.plans, kPlanThreads, 0, s>>>(t);
+  band_plan_kernel<MAXP><<<t.plans, kPlanThreads, smem, s>>>(t);
   ktimer_end(s);
 }
 

@@ -65,11 +65,14 @@ void band_prepare(cudaStream_t s, const BandTable<MAXP>& t);
 template <int MODE, int MAXP>
 void band_simt(cudaStream_t s, const BandTable<MAXP>& t);
 
-// a whole pass on the tensor cores (fot_tc.cu): picks the tile width from eps, finishes the
-// table, plans and launches; tiles outside the tilt bound take the CUDA-core sums inside the
-// same kernel, and a pass where no tile can meet the bound runs band_simt.  Returns the
-// number of kernels launched.
+// tile width of the tensor-core pass for kernel constant c: 64, 32, 16, or 0 (CUDA cores)
+int tc_width_for(float c);
+
+// a whole pass on the tensor cores (fot_tc.cu) at tile width tw (every problem of the table
+// must have tc_width_for(c) == tw): finishes the table, plans and launches; tiles outside the
+// tilt bound take CUDA-core sums inside the same kernel, and tw = 0 runs band_simt.  Returns
+// the number of kernels launched.
 template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, BandTable<MAXP>& t);
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw);
 
 }  // namespace fot

@@ -165,7 +165,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
         continue;
       }
       const float mref = (float)lo[rr] + halfW;
-      out[rr] = alpha[rr] + 2.f * kap * (mref - (float)kc) * c + log2f(acc[rr]);
+      out[rr] = __fadd_rn(fmaf(2.f * kap * (mref - (float)kc), c, alpha[rr]), log2f(acc[rr]));
     }
   } else {
     // 4. exact log-sum-exp over each row's own window; the two halves step through their
@@ -196,7 +196,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
           __syncwarp();
         }
       }
-      if (alpha[rr] != -INFINITY && mx != -INFINITY) out[rr] = mx + log2f(sum);
+      if (alpha[rr] != -INFINITY && mx != -INFINITY) out[rr] = __fadd_rn(mx, log2f(sum));
     }
   }
 
@@ -210,13 +210,13 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
     if (MODE == kBandLse) {
       a.y[yi] = out[rr];
     } else {
-      const float s = out[rr] * kLn2;
+      const float s = __fmul_rn(out[rr], kLn2);
       const float lm = a.lmarg[yi];
       float pot;
       if (lm == -INFINITY) {
         pot = -INFINITY;
       } else {
-        pot = a.eps * (lm - s);
+        pot = __fmul_rn(a.eps, __fsub_rn(lm, s));
         if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
       }
       a.y[yi] = pot;

@@ -56,11 +56,13 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
     set_problem_simt(c, g[q], G[q], c->psi, psi0);
     k += 3;
   }
-  BandTable<kMaxBatch>* t1 = new BandTable<kMaxBatch>();
-  BandTable<kMaxBatch>* t2 = new BandTable<kMaxBatch>();
+  // one table per pass and tile width: a problem runs the same kernels as its single solve
+  static const int kWidths[4] = {64, 32, 16, 0};
+  BandTable<kMaxBatch>* tab = new BandTable<kMaxBatch>();
+  std::vector<BandArgs> p1(n), p2(n);
+  std::vector<int> width(n);
   for (int it = 0; it < iters; ++it) {
     for (int half = 0; half < 2; ++half) {
-      t1->n = t2->n = n;
       for (int q = 0; q < n; ++q) {
         fot_ctx* c = b->ctx[q];
         const double e = eps[(size_t)q * n_eps + (n_eps == 1 ? 0 : it)];
@@ -73,25 +75,33 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         a2.lmarg = half == 0 ? c->la : c->lb;
         a2.logsum = (half == 0 && it == iters - 1) ? c->S_last : nullptr;
         if (use_tc) a1.tc_terms = a2.tc_terms = tc_terms_ptr(c);
-        t1->p[q] = a1;
-        t2->p[q] = a2;
+        p1[q] = a1;
+        p2[q] = a2;
+        width[q] = use_tc ? tc_width_for(a1.c) : -1;
       }
-      if (use_tc) {
-        k += tc_pass<0>(st, *t1);
-        k += tc_pass<1>(st, *t2);
-      } else {
-        band_table_finish(*t1);
-        band_prepare(st, *t1);
-        band_simt<0>(st, *t1);
-        band_table_finish(*t2);
-        band_prepare(st, *t2);
-        band_simt<1>(st, *t2);
-        k += 4;
+      for (int pass = 0; pass < 2; ++pass) {
+        const std::vector<BandArgs>& pa = pass == 0 ? p1 : p2;
+        for (int wi = 0; wi < (use_tc ? 4 : 1); ++wi) {
+          tab->n = 0;
+          for (int q = 0; q < n; ++q)
+            if (width[q] == (use_tc ? kWidths[wi] : -1)) tab->p[tab->n++] = pa[q];
+          if (tab->n == 0) continue;
+          if (use_tc) {
+            k += pass == 0 ? tc_pass<0>(st, *tab, kWidths[wi]) : tc_pass<1>(st, *tab, kWidths[wi]);
+          } else {
+            band_table_finish(*tab);
+            band_prepare(st, *tab);
+            if (pass == 0)
+              band_simt<0>(st, *tab);
+            else
+              band_simt<1>(st, *tab);
+            k += 2;
+          }
+        }
       }
     }
   }
-  delete t1;
-  delete t2;
+  delete tab;
   for (int q = 0; q < n; ++q) {
     fot_ctx* c = b->ctx[q];
     c->stream = b->stream;

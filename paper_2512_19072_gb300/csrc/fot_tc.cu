@@ -106,26 +106,33 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int* e
   return false;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // .x = a (low half), .y = b
-  return *reinterpret_cast<const uint32_t*>(&v);
+// split 8 consecutive values into hi / lo BF16 parts (hi = round(v), lo = round(v - hi)) and
+// store one 16-byte row of a core matrix for each (plain shared-memory stores; the caller
+// fences them for the tensor core's async proxy)
+__device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p, unsigned char* lo_p) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 hf = __bfloat1622float2(h2);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+    hw[i] = *reinterpret_cast<const uint32_t*>(&h2);
+    lw[i] = *reinterpret_cast<const uint32_t*>(&l2);
+  }
+  *reinterpret_cast<uint4*>(hi_p) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(lo_p) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
-// split 8 consecutive values into hi / lo BF16 parts and store one 16-byte row of a core
-// matrix for each
-__device__ __forceinline__ void store_split8(const float* v, uint32_t hi_addr, uint32_t lo_addr) {
-  float h[8], l[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
-    l[i] = v[i] - h[i];
+// CUDA-core window sums of a declined tile (kept out of line: rarely run, and large)
+template <int MODE, int TN>
+__device__ __noinline__ void tc_declined_tile(const BandArgs& a, int rw, int tile, int k0, float* sAw) {
+  if (TN == kBT) {
+    band_item<MODE, 0>(a, rw, tile, k0, sAw);
+    band_item<MODE, 1>(a, rw, tile, k0, sAw);
+  } else {
+    for (int q = 0; q < TN / kBT && k0 + q * kBT < a.len; ++q)
+      band_item<MODE, 1, true>(a, rw, tile, k0 + q * kBT, sAw);
   }
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(hi_addr),
-               "r"(pack_bf16(h[0], h[1])), "r"(pack_bf16(h[2], h[3])), "r"(pack_bf16(h[4], h[5])),
-               "r"(pack_bf16(h[6], h[7])) : "memory");
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" :: "r"(lo_addr),
-               "r"(pack_bf16(l[0], l[1])), "r"(pack_bf16(l[2], l[3])), "r"(pack_bf16(l[4], l[5])),
-               "r"(pack_bf16(l[6], l[7])) : "memory");
 }
 
 template <int MODE, int TN, int MAXP>
@@ -178,35 +185,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   const bool take = s_wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
   if (!take) {                                          // CTA-uniform
     const int rw = r0 + warp * 2 * kBR;                 // this warp's 16 rows
-    if (rw < a.n_rows) {
-      float* sAw = reinterpret_cast<float*>(smem) + warp * 2 * kSA;
-      if (TN == kBT) {
-        band_item<MODE, 0>(a, rw, tile, k0, sAw);
-        band_item<MODE, 1>(a, rw, tile, k0, sAw);
-      } else {
-        for (int q = 0; q < TN / kBT && k0 + q * kBT < a.len; ++q)
-          band_item<MODE, 1, true>(a, rw, tile, k0 + q * kBT, sAw);
-      }
-    }
+    if (rw < a.n_rows)
+      tc_declined_tile<MODE, TN>(a, rw, tile, k0, reinterpret_cast<float*>(smem) + warp * 2 * kSA);
     return;
   }
   if (tid == 0) atomicAdd(tc_terms, (unsigned long long)W * kTN * kTM);
 
-  // tensor memory for the 128 x 32 FP32 accumulator, and the two stage barriers
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem_d = tmem_base_sh;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t idesc = instr_desc(kTM, kTN);
   const float halfW = 0.5f * (float)W;
@@ -243,18 +227,34 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
       }
     }
   };
-  load_x(0);
+  load_x(0);                                // in flight while the CTA sets up
+
+  // tensor memory for the 128 x TN FP32 accumulator, and the two stage barriers
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_base_sh;
   int issued = 0;                           // chunks whose MMAs were issued and committed
-  for (int ch = 0; ch < nchunk && ok; ++ch) {
+  for (int ch = 0; ch < nchunk; ++ch) {
     const int s = ch & 1;
-    if (ch >= 2) {
-      ok = mbar_wait(smem_u32(&mbar[s]), ((ch - 2) >> 1) & 1, a.err);   // stage free again
-      ok = __syncthreads_and(ok);           // one decision for the whole CTA
-    }
-    if (!ok) break;
+    // stage free again (the MMAs of chunk ch - 2 have read it); a thread that gave up writes
+    // nothing, and the barrier below makes the decision the CTA's
+    const bool ok_w = ch < 2 || mbar_wait(smem_u32(&mbar[s]), ((ch - 2) >> 1) & 1, a.err);
     const uint32_t st = sbase + s * kStageBytes;
     const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
+    unsigned char* const stp = smem + s * kStageBytes;     // the same stage, generic pointer
     const int m0 = ch * kKC;
+    if (ok_w) {
     float xv[32];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
       }
       const int kg = ah * 4 + g;                          // core-matrix column in the stage
       const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
-      store_split8(v, sAhi + off, sAlo + off);
+      store_split8(v, stp + off, stp + kABytes + off);
     }
     // B: 8 window positions of output bn per core row
 #pragma unroll
@@ -291,10 +291,12 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
         v[i] = ex2(fmaf(bt2, mp, btk));
       }
       const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
-      store_split8(v, sBhi + off, sBlo + off);
+      store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
     }
+    }                                        // ok_w
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    ok = __syncthreads_and(ok_w);            // stores visible to the MMA; one decision
+    if (!ok) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -406,6 +408,10 @@ int tc_create(fot_ctx* c) {
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 32, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 32, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
@@ -436,27 +442,27 @@ int64_t tc_terms(fot_ctx* c) {
   return (int64_t)v;
 }
 
-// Tile width of a tensor-core pass from the largest c of the table's problems:
-//  64 when a 64-wide tile is expected to meet the tilt bound: its window spans the tile plus
-//     about sqrt(kCut / c) on each side (where the Gaussian kernel alone falls by 2^-kCut),
-//     rounded up to whole stages, and |kap| W c <= kTiltMaxTC at |kap| = 32;
-//  16 when a 16-wide tile can meet it at all (a taken tile has W >= kKC);
-//   0 when neither: the pass runs the CUDA-core kernels.
-template <int MAXP>
-int tc_width(const BandTable<MAXP>& t) {
-  float cmax = 0.f;
-  for (int q = 0; q < t.n; ++q) cmax = fmaxf(cmax, t.p[q].c);
-  const float w64 = 64.f + 2.f * sqrtf(kCut / cmax);
-  const float w64r = ceilf(w64 / (float)kKC) * (float)kKC;
-  if (32.f * w64r * cmax <= kTiltMaxTC && 32.f * 32.f * cmax <= 32.f) return 64;
-  if ((float)(kBT / 2) * (float)kKC * cmax <= kTiltMaxTC) return 16;
+// Tile width of a tensor-core pass for a problem with kernel constant c: the widest TN in
+// {64, 32} whose tile is expected to meet the tilt bound |kap| W c <= kTiltMaxTC with room to
+// spare: W is taken as twice the window of a smooth potential (the tile plus sqrt(kCut / c) on
+// each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to whole
+// stages, since the hull of a tile's windows grows where the transport map jumps across
+// zero-mass gaps; else 16 when a 16-wide tile can meet the bound at all (a taken tile has
+// W >= kKC); else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
+int tc_width_for(float c) {
+  for (int tn = 64; tn >= 32; tn /= 2) {
+    const float w = (float)tn + 2.f * sqrtf(kCut / c);
+    const float wr = 2.f * ceilf(w / (float)kKC) * (float)kKC;
+    if ((float)(tn / 2) * wr * c <= kTiltMaxTC && (float)(tn / 2) * (float)(tn / 2) * c <= 32.f) return tn;
+  }
+  if ((float)(kBT / 2) * (float)kKC * c <= kTiltMaxTC) return 16;
   return 0;
 }
 
+// tw: the tile width every problem of the table uses (tc_width_for of its c)
 template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, BandTable<MAXP>& t) {
-  const int tw = tc_width(t);
-  for (int q = 0; q < t.n; ++q) t.p[q].tile_w = tw == 64 ? 64 : kBT;
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw) {
+  for (int q = 0; q < t.n; ++q) t.p[q].tile_w = tw == 0 ? kBT : tw;
   band_table_finish(t);
   band_prepare(s, t);
   if (tw == 0) {
@@ -466,6 +472,8 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t) {
   ktimer_begin(s, kKTensor);
   if (tw == 64)
     tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreads, TcShape<64>::kSmemBytes, s>>>(t);
+  else if (tw == 32)
+    tc_pass_kernel<MODE, 32, MAXP><<<t.ctas, kThreads, TcShape<32>::kSmemBytes, s>>>(t);
   else
     tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreads, TcShape<16>::kSmemBytes, s>>>(t);
   ktimer_end(s);
@@ -473,10 +481,10 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t) {
 }
 
 unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
-template int tc_pass<0, 1>(cudaStream_t, BandTable<1>&);
-template int tc_pass<1, 1>(cudaStream_t, BandTable<1>&);
-template int tc_pass<0, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&);
-template int tc_pass<1, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&);
+template int tc_pass<0, 1>(cudaStream_t, BandTable<1>&, int);
+template int tc_pass<1, 1>(cudaStream_t, BandTable<1>&, int);
+template int tc_pass<0, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int);
+template int tc_pass<1, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int);
 
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 
@@ -489,13 +497,14 @@ void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double ep
   t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
   t.p[0].y = c->R;
   t.p[0].tc_terms = ts->tc_terms;
-  int k = tc_pass<0>(c->stream, t);
+  const int tw = tc_width_for(t.p[0].c);
+  int k = tc_pass<0>(c->stream, t, tw);
   t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
   t.p[0].y = pot_out;
   t.p[0].lmarg = lmarg;
   t.p[0].logsum = logsum;
   t.p[0].tc_terms = ts->tc_terms;
-  k += tc_pass<1>(c->stream, t);
+  k += tc_pass<1>(c->stream, t, tw);
   c->launches += k;
 }
 
