@@ -8,10 +8,9 @@
 // band_plan_kernel (one CTA per row) and leave (alpha, lo, window length) per (row, tile);
 // steps 3-4 run in band_pass_kernel.
 //
-// 1. Offset at every tile centre kc = k0 + 8: a term alpha_r = e_r(m_r, kc) within 16 (log2
-//    units) of max_m e_r(m, kc), e_r(m, o) = x_r[m] - (o - m)^2 c, found by scanning only the
-//    32-wide chunks of m whose upper bound (chunk maximum of x, nearest distance) exceeds the
-//    best term found so far by more than that.
+// 1. Offset at every tile centre kc = k0 + 8: alpha_r = max_m e_r(m, kc) (up to rounding),
+//    e_r(m, o) = x_r[m] - (o - m)^2 c, and its argmax, from the upper convex hulls of the
+//    32-wide chunks (see band_plan_kernel).
 // 2. A provable window: every o in the tile has max_m e_r(m, o) >= LB_r, with LB_r the
 //    value of the centre's argmax term at the worse tile end.  A 32-wide chunk of m whose
 //    upper bound (chunk maximum of x, nearest distance) over the whole tile is below
@@ -21,7 +20,7 @@
 //      e_r(m, o) = [x_r[m] - (kc - m)^2 c - alpha_r] + [2 kap (m - Mref_r) c - kap^2 c]
 //                  + alpha_r + 2 kap (Mref_r - kc) c,
 //    so  sum_m 2^e = 2^(alpha_r + 2 kap (Mref_r - kc) c) * sum_m' A[r][m'] B[m'][kap]
-//    with A[r][m'] = 2^(e_r(lo_r + m', kc) - alpha_r) <= 2^16 (one exponential per row and
+//    with A[r][m'] = 2^(e_r(lo_r + m', kc) - alpha_r) <= 1 (one exponential per row and
 //    window position, shared by the tile's outputs) and B[m'][kap] = 2^(2 kap (m' - W/2) c -
 //    kap^2 c), the same for every row once each row's window is indexed from its own start
 //    lo_r (Mref_r = lo_r + W/2).  This is a GEMM over the window, done with FFMAs; the
@@ -38,42 +37,46 @@ namespace fot {
 // Per (row, tile) plan (tiles of tile_w = 16, 32 or 64 outputs): centre offset alpha, window
 // start lo and length wl.  One CTA of four warps per row.  The row is staged in shared memory
 // as z[m] = x[m] * scale - u^2 c (u = m mod 32, one pad word per 32-wide chunk), with the
-// maxima of x * scale over 32-wide chunks and over 8-wide sub-chunks.  Each warp then plans
-// tiles one at a time:
-//   a. alpha: with d0 = kc - 32 j, e(32 j + u, kc) = z[32 j + u] + 2 c d0 u - c d0^2.  Lane l
-//      takes element l of the chunk holding the centre kc, and every sub-chunk it owns whose
-//      upper bound (sub-chunk maximum less the nearest squared distance times c) exceeds that
-//      chunk's best term by more than kAlphaSlack; one warp argmax over the lanes' best terms
-//      gives alpha and its index.  Every sub-chunk left out is bounded by alpha + kAlphaSlack,
-//      so alpha is a term within kAlphaSlack of the maximum: it only scales the window sums'
-//      operands (A <= 2^kAlphaSlack instead of <= 1, far from overflow, and the largest term
-//      of every output keeps A >= 2^-2 kTiltMax), and the window bound below needs a term.
+// chunk maxima of x * scale.
+//   a. alpha: with d0 = kc - 32 j, e(32 j + u, kc) = z[32 j + u] + t u - c d0^2, t = 2 c d0,
+//      so the maximum of chunk j at any centre is the support function of the upper convex
+//      hull of the points (u, z[32 j + u]) at slope t.  One thread per chunk builds that hull
+//      (monotone chain, at most 32 vertices) and the slopes of its edges, which decrease; a
+//      query is a binary search for the first edge slope <= -t.  A warp takes one tile at a
+//      time, lanes query their chunks, and a warp argmax gives alpha (the maximum at kc up to
+//      rounding) and its index.
 //   b. the window of step 2 above: the first and the last 32-wide chunk whose bound over the
 //      tile reaches LB - kCut (one ballot per 32 chunks).
 constexpr int kPlanThreads = 128;
-constexpr int kSub = 8;                       // sub-chunk width
-constexpr float kAlphaSlack = 16.f;           // alpha may sit this far (log2) below the maximum
+
+// shared memory of one row: z[n_chunks * 33], cm[n_chunks], hull vertex count[n_chunks],
+// edge slopes[n_chunks * 33], vertex positions[n_chunks * 36] (bytes); the odd word strides
+// keep threads that work on different chunks on different banks
+constexpr int kHullS = kCW + 1;      // slope row stride (floats)
+constexpr int kHullU = kCW + 4;      // vertex row stride (bytes)
+__host__ __device__ inline size_t plan_smem_bytes(int n_chunks) {
+  return (size_t)n_chunks * (kCW + 1 + 1 + 1 + kHullS) * 4 + (size_t)n_chunks * kHullU;
+}
 
 template <int MAXP>
 __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
-  extern __shared__ float s_plan[];   // [n_chunks * 33] z, [n_chunks] chunk maxima, [4 n_chunks] sub
+  extern __shared__ __align__(16) float s_plan[];
   const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, (int)blockIdx.x)];
   if (error_latched(a.err)) return;                       // CTA-uniform
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = (int)blockIdx.x - a.plan_base;
-  const int T = a.n_tiles, len = a.len, nch = a.n_chunks;
-  const int nsub = nch * (kCW / kSub);
-  const int nwords = (nch + 31) / 32, nswords = (nsub + 31) / 32;
+  const int T = a.n_tiles, len = a.len, nch = a.n_chunks, tw = a.tile_w;
   const float c = a.c, sc = a.x_scale;
   const float* xr = a.x + (size_t)row * len;
   float* s_z = s_plan;
-  float* s_cm = s_plan + nch * (kCW + 1);
-  float* s_c8 = s_cm + nch;
-  // stage: each warp takes whole chunks, four at a time (lane = position in the chunk; the
-  // four loads are issued together); max(x) * sc equals max(x * sc) since sc > 0 and rounding
-  // is monotone
+  float* s_cm = s_z + nch * (kCW + 1);
+  int* s_hn = reinterpret_cast<int*>(s_cm + nch);
+  float* s_hs = reinterpret_cast<float*>(s_hn + nch);                          // [j][k] edge k slope
+  unsigned char* s_hu = reinterpret_cast<unsigned char*>(s_hs + nch * kHullS);   // [j][k] vertex u
+
+  // stage: each warp takes whole chunks, four at a time (lane = position in the chunk)
   const float uc = -(float)(lane * lane) * c;
-  for (int j0 = warp * 4; j0 < nch; j0 += nw * 4) {
+  for (int j0 = warp * 4; j0 < nch; j0 += kPlanThreads / 8) {
     float v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -85,50 +88,67 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
       if (j0 + q >= nch) break;                           // warp-uniform
       s_z[(j0 + q) * (kCW + 1) + lane] = __fadd_rn(v[q], uc);   // no contraction: the same
                                                                   // rounding in every instance
-      float mx = v[q];
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
-      if ((lane & (kSub - 1)) == 0) s_c8[(j0 + q) * (kCW / kSub) + lane / kSub] = mx;
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+      const float mx = warp_max(v[q]);
       if (lane == 0) s_cm[j0 + q] = mx;
     }
   }
   __syncthreads();
+  // upper hulls, one thread per chunk (the padded rows keep the threads on different banks)
+  for (int j = tid; j < nch; j += kPlanThreads) {
+    const float* zs = &s_z[j * (kCW + 1)];
+    unsigned char* hu = &s_hu[j * kHullU];
+    float* hs = &s_hs[j * kHullS];
+    int n = 0;
+    for (int u = 0; u < kCW; ++u) {
+      const float zu = zs[u];
+      if (zu == -INFINITY) continue;
+      // pop while the last vertex lies on or below the segment from the one before it to u
+      while (n >= 2) {
+        const int u0 = hu[n - 2], u1 = hu[n - 1];
+        const float z0 = zs[u0], z1 = zs[u1];
+        if ((z1 - z0) * (float)(u - u0) <= (zu - z0) * (float)(u1 - u0))
+          --n;
+        else
+          break;
+      }
+      hu[n++] = (unsigned char)u;
+    }
+    for (int k = 0; k + 1 < n; ++k)
+      hs[k] = (zs[hu[k + 1]] - zs[hu[k]]) / (float)(hu[k + 1] - hu[k]);
+    s_hn[j] = n;
+  }
+  __syncthreads();
+
   const size_t np = (size_t)a.n_rows * T;
   float* p_alpha = a.plan;
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
-  const int tw = a.tile_w;
-
-  for (int t = warp; t < T; t += nw) {
+  const int nwords = (nch + 31) / 32;
+  for (int t = warp; t < T; t += kPlanThreads / 32) {
     const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
-    // a. element `lane` of the centre's chunk, then this lane's qualifying sub-chunks
-    const int jc = min(kc, len - 1) / kCW;
-    const float dc = (float)(kc - jc * kCW);
-    float best = fmaf((float)lane, 2.f * c * dc, s_z[jc * (kCW + 1) + lane]);
-    best = fmaf(-dc * dc, c, best);
-    int arg = jc * kCW + lane;
-    const float floor_ = warp_max(best) + kAlphaSlack;  // sub-chunks at or below: left out
-#pragma unroll 1
-    for (int w = 0; w < nswords; ++w) {
-      const int sj = 32 * w + lane;
-      const int m0 = sj * kSub, m1 = min(m0 + kSub, len) - 1;
-      const int d = m0 > kc ? m0 - kc : (m1 < kc ? kc - m1 : 0);
-      const float c8 = sj < nsub ? s_c8[sj] : -INFINITY;
-      if (sj / (kCW / kSub) != jc && fmaf(-(float)d * (float)d, c, c8) > floor_) {
-        const int j = sj / (kCW / kSub), u0 = m0 - j * kCW;
+    // a. the maximum at kc: each lane its chunks, then a warp argmax
+    float best = -INFINITY;
+    int arg = 0x7fffffff;
+    for (int w = 0; w < nwords; ++w) {
+      const int j = 32 * w + lane;
+      const int n = j < nch ? s_hn[j] : 0;
+      if (n > 0) {
         const float d0 = (float)(kc - j * kCW);
         const float t2 = 2.f * c * d0;
-        const float* zs = &s_z[j * (kCW + 1) + u0];
-#pragma unroll
-        for (int v = 0; v < kSub; ++v) {
-          const float e = fmaf(-d0 * d0, c, fmaf((float)(u0 + v), t2, zs[v]));
-          if (e > best) {
-            best = e;
-            arg = m0 + v;
-          }
+        const float* hs = &s_hs[j * kHullS];
+        int lo = 0, hi = n - 1;                           // first edge with slope <= -t2
+        while (lo < hi) {
+          const int md = (lo + hi) >> 1;
+          if (hs[md] <= -t2)
+            hi = md;
+          else
+            lo = md + 1;
+        }
+        const int u = s_hu[j * kHullU + lo];
+        const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
+        if (v > best) {
+          best = v;
+          arg = j * kCW + u;
         }
       }
     }
@@ -149,14 +169,12 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
     const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
     const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
     int wlo = -1, whi = -1;
-#pragma unroll 1
     for (int w = 0; w < nwords; ++w) {
       const int j = 32 * w + lane;
       const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
       const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
       const float cmj = j < nch ? s_cm[j] : -INFINITY;
-      const bool in = fmaf(-(float)d * (float)d, c, cmj) >= lb - kCut;
-      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      const unsigned bal = __ballot_sync(0xffffffffu, fmaf(-(float)d * (float)d, c, cmj) >= lb - kCut);
       if (bal) {
         if (wlo < 0) wlo = 32 * w + __ffs(bal) - 1;
         whi = 32 * w + 31 - __clz(bal);
@@ -214,9 +232,8 @@ void band_table_finish(BandTable<MAXP>& t) {
 
 template <int MAXP>
 void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
-  int max_chunks = 1;
-  for (int q = 0; q < t.n; ++q) max_chunks = std::max(max_chunks, t.p[q].n_chunks);
-  const size_t smem = (size_t)max_chunks * (kCW + 2 + kCW / kSub) * sizeof(float);
+  size_t smem = 0;
+  for (int q = 0; q < t.n; ++q) smem = std::max(smem, plan_smem_bytes(t.p[q].n_chunks));
   ktimer_begin(s, kKPlan);
   band_plan_kernel<MAXP><<<t.plans, kPlanThreads, smem, s>>>(t);
   ktimer_end(s);

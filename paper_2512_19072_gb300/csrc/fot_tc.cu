@@ -6,12 +6,17 @@
 //     B[m'][kap] = 2^(2 kap (m' - W/2) c - kap^2 c)                     (same for all rows)
 // after which y[kc + kap][r] = alpha_r + 2 kap (lo_r + W/2 - kc) c + log2 C[r][kap] (the
 // per-row max-offsets of Sec. 3.1's Toeplitz contraction, plus the tilt).  One CTA computes
-// a 128-row x TN-output tile (TN = 16 or 64) with tcgen05.mma (M = 128, N = TN, K = 16 per
-// instruction), the FP32 accumulator in tensor memory.  A 64-wide tile needs one A operand
-// (one exponential per row and window position) for four times the outputs of a 16-wide
-// one; it is used when eps is large enough for the tilt bound at |kap| <= 32.  The operands are generated in shared memory by all
-// 256 threads (one exponential per element) in the canonical no-swizzle K-major layout,
-// double-buffered against the MMAs through mbarriers that tcgen05.commit arrives on.
+// a 128-row x TN-output tile (TN = 16, 32 or 64) with tcgen05.mma (M = 128, N = TN, K = 16
+// per instruction), the FP32 accumulator in tensor memory.  A wider tile shares one A operand
+// (one exponential per row and window position) between more outputs; the host picks the
+// widest one whose tilt bound the problem's eps allows.
+//
+// Warp roles: eight producer warps generate the operands of each 64-position stage in shared
+// memory (canonical no-swizzle K-major layout) and arrive on the stage's "full" mbarrier; one
+// more warp owns the tensor memory and issues the stage's MMAs once all producers have
+// arrived, committing to the stage's "empty" mbarrier, which the producers wait on before
+// reusing it (two stages).  A last commit signals the epilogue, in which the producers read
+// the accumulator (the potential-update pass prefetches its marginals during the last MMAs).
 //
 // Precision: each operand is split into two BF16 parts, v = hi + lo (hi = bf16(v),
 // lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
@@ -20,11 +25,11 @@
 // A CTA uses the tensor cores only when the tilt bound holds for the common window length W
 // of its 128 rows: |kap| W c <= 48 with |kap| <= TN / 2.  Then every output's largest term has
 // A >= 2^-96, and the A values that flush below 2^-126 add less than W 2^-30 relative: below
-// the 2^-16 of the split-BF16 products.  Otherwise its eight warps compute the tile with the
-// CUDA-core window sums of the banded pass (16 rows each; for a 64-wide tile the exact window
-// sums over the tile's window, which covers the windows of its 16-wide parts).  Every mbarrier wait is
-// bounded: on time-out the kernel latches FOT_ETIMEOUT, stops issuing, frees its tensor
-// memory and returns.
+// the 2^-16 of the split-BF16 products.  Otherwise its producer warps compute the tile with the
+// CUDA-core window sums of the banded pass (16 rows each; for a wider tile the exact window
+// sums over the tile's window, which covers the windows of its 16-wide parts).  Every mbarrier
+// wait is bounded: on time-out the kernel latches FOT_ETIMEOUT, stops issuing, waits (again
+// bounded) for the MMAs in flight, frees its tensor memory and returns.
 #include "fot_band_item.cuh"
 
 #include <cuda_bf16.h>
@@ -37,7 +42,8 @@ namespace {
 
 constexpr int kTM = 128;            // rows per CTA (MMA M, TMEM lanes)
 constexpr int kKC = 64;             // window positions per pipeline stage
-constexpr int kThreads = 256;
+constexpr int kProducerWarps = 8;   // operand producers (256 threads)
+constexpr int kThreadsTC = kProducerWarps * 32 + 32;   // + the MMA-issuing warp
 constexpr float kTiltMaxTC = 48.f;
 constexpr int kSpin = 1 << 20;      // bounded mbarrier polls
 
@@ -89,6 +95,10 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(mbar), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -136,13 +146,13 @@ __device__ __noinline__ void tc_declined_tile(const BandArgs& a, int rw, int til
 }
 
 template <int MODE, int TN, int MAXP>
-__global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+__global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   constexpr int kTN = TN;
   constexpr int kStageBytes = TcShape<TN>::kStageBytes;
   constexpr int kBBytes = TcShape<TN>::kBBytes;
   constexpr uint32_t kTmemCols = TcShape<TN>::kTmemCols;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t full[2], empty[2], done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ float s_alpha[kTM];
   __shared__ int s_lo[kTM];
@@ -160,7 +170,6 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   const float* __restrict__ p_alpha = a.plan;
   const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
   const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
-  unsigned long long* tc_terms = a.tc_terms;
 
   // per-row plan and the common window length
   if (tid == 0) s_wmax = 0;
@@ -184,30 +193,28 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   const float kmax = (float)(kTN / 2);
   const bool take = s_wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
   if (!take) {                                          // CTA-uniform
-    const int rw = r0 + warp * 2 * kBR;                 // this warp's 16 rows
-    if (rw < a.n_rows)
+    const int rw = r0 + warp * 2 * kBR;                 // producer warp w: rows rw .. rw + 15
+    if (warp < kProducerWarps && rw < a.n_rows)
       tc_declined_tile<MODE, TN>(a, rw, tile, k0, reinterpret_cast<float*>(smem) + warp * 2 * kSA);
     return;
   }
-  if (tid == 0) atomicAdd(tc_terms, (unsigned long long)W * kTN * kTM);
+  if (tid == 0) atomicAdd(a.tc_terms, (unsigned long long)W * kTN * kTM);
 
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t idesc = instr_desc(kTM, kTN);
   const float halfW = 0.5f * (float)W;
-  bool ok = true;
+  const int nchunk = W / kKC;
+  const bool producer = warp < kProducerWarps;
 
   // producer roles: A row r = tid % 128, half h = tid / 128 (32 window positions each);
   // B: core rows q = tid, tid + 256, ... of TN outputs x 8 groups of 8 positions
-  const int ar = tid & (kTM - 1), ah = tid >> 7;
+  const int ar = tid & (kTM - 1), ah = (tid >> 7) & 1;
   const float a_alpha = s_alpha[ar];
   const int a_lo = s_lo[ar];
   const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
-
-  const int nchunk = W / kKC;
   // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
   // multiple of 32 and each chunk starts at a multiple of 64, so the float4 loads are
   // aligned; positions at or beyond len read -inf (the kernel skips rows without mass).
-  const bool a_live = a_alpha != -INFINITY;
+  const bool a_live = producer && a_alpha != -INFINITY;
   // the 16-byte vector load needs the row base aligned too: x + row * len is 16-byte aligned
   // only when row * len is a multiple of 4 (window starts are multiples of 32)
   const bool vec_ok = (reinterpret_cast<uintptr_t>(xr) & 15u) == 0;
@@ -227,114 +234,137 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
       }
     }
   };
-  load_x(0);                                // in flight while the CTA sets up
+  if (producer) load_x(0);                  // in flight while the CTA sets up
 
-  // tensor memory for the 128 x TN FP32 accumulator, and the two stage barriers
-  if (warp == 0) {
+  // the MMA warp owns the tensor memory (128 x TN FP32 accumulator) and the barriers:
+  // full[s] (256 producer arrivals: stage s written), empty[s] (the commit of the MMAs that
+  // read stage s), done (the commit after the last chunk)
+  if (warp == kProducerWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (lane == 0) {
+      mbar_init(smem_u32(&full[0]), kProducerWarps * 32);
+      mbar_init(smem_u32(&full[1]), kProducerWarps * 32);
+      mbar_init(smem_u32(&empty[0]), 1);
+      mbar_init(smem_u32(&empty[1]), 1);
+      mbar_init(smem_u32(&done), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_d = tmem_base_sh;
-  int issued = 0;                           // chunks whose MMAs were issued and committed
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int s = ch & 1;
-    // stage free again (the MMAs of chunk ch - 2 have read it); a thread that gave up writes
-    // nothing, and the barrier below makes the decision the CTA's
-    const bool ok_w = ch < 2 || mbar_wait(smem_u32(&mbar[s]), ((ch - 2) >> 1) & 1, a.err);
-    const uint32_t st = sbase + s * kStageBytes;
-    const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
-    unsigned char* const stp = smem + s * kStageBytes;     // the same stage, generic pointer
-    const int m0 = ch * kKC;
-    if (ok_w) {
-    float xv[32];
+  bool ok = true;
+
+  if (!producer) {
+    // MMA warp: lane 0 issues each stage's MMAs once its 256 producers have arrived
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(kTM, kTN);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const int s = ch & 1;
+        if (!mbar_wait(smem_u32(&full[s]), (ch >> 1) & 1, a.err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = sbase + s * kStageBytes;
+        const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      xv[4 * q] = xq[q].x;
-      xv[4 * q + 1] = xq[q].y;
-      xv[4 * q + 2] = xq[q].z;
-      xv[4 * q + 3] = xq[q].w;
-    }
-    if (ch + 1 < nchunk) load_x(m0 + kKC);
-    // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
-    const float dbase = (float)(kc - (a_lo + m0 + ah * 32));
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float d = dbase - (float)(g * 8 + i);
-        v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - (a_live ? a_alpha : 0.f));   // -inf -> 0
+        for (int ks = 0; ks < kKC / 16; ++ks) {
+          const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, 1024);
+          const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, 1024);
+          const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, 1024);
+          const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, 1024);
+          mma_bf16(tmem_d, dAh, dBh, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
+          mma_bf16(tmem_d, dAh, dBl, idesc, 1u);
+          mma_bf16(tmem_d, dAl, dBh, idesc, 1u);
+        }
+        mma_commit(smem_u32(&empty[s]));
       }
-      const int kg = ah * 4 + g;                          // core-matrix column in the stage
-      const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
-      store_split8(v, stp + off, stp + kABytes + off);
+      // arrives when every MMA issued above has completed; the producers wait on it before
+      // reading the accumulator, and this thread before the tensor memory is released
+      mma_commit(smem_u32(&done));
+      ok = mbar_wait(smem_u32(&done), 0, a.err) && ok;
     }
-    // B: 8 window positions of output bn per core row
-#pragma unroll
-    for (int q = tid; q < kTN * (kKC / 8); q += kThreads) {
-      const int bn = q % kTN, bq = q / kTN;
-      const float bkap = (float)(bn - kTN / 2);
-      const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
-      float v[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float mp = (float)(m0 + bq * 8 + i) - halfW;
-        v[i] = ex2(fmaf(bt2, mp, btk));
+    __syncwarp();
+  } else {
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int s = ch & 1;
+      // stage free again: the MMAs of chunk ch - 2 (its previous use) have completed
+      if (ch >= 2 && !mbar_wait(smem_u32(&empty[s]), ((ch - 2) >> 1) & 1, a.err)) {
+        ok = false;
+        break;
       }
-      const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
-      store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
-    }
-    }                                        // ok_w
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    ok = __syncthreads_and(ok_w);            // stores visible to the MMA; one decision
-    if (!ok) break;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* const stp = smem + s * kStageBytes;
+      const int m0 = ch * kKC;
+      float xv[32];
 #pragma unroll
-      for (int ks = 0; ks < kKC / 16; ++ks) {
-        const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, 1024);
-        const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, 1024);
-        const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, 1024);
-        const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, 1024);
-        mma_bf16(tmem_d, dAh, dBh, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
-        mma_bf16(tmem_d, dAh, dBl, idesc, 1u);
-        mma_bf16(tmem_d, dAl, dBh, idesc, 1u);
+      for (int q = 0; q < 8; ++q) {
+        xv[4 * q] = xq[q].x;
+        xv[4 * q + 1] = xq[q].y;
+        xv[4 * q + 2] = xq[q].z;
+        xv[4 * q + 3] = xq[q].w;
       }
-      mma_commit(smem_u32(&mbar[s]));
+      if (ch + 1 < nchunk) load_x(m0 + kKC);
+      // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
+      const float dbase = (float)(kc - (a_lo + m0 + ah * 32));
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float d = dbase - (float)(g * 8 + i);
+          v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - (a_live ? a_alpha : 0.f));   // -inf -> 0
+        }
+        const int kg = ah * 4 + g;                        // core-matrix column in the stage
+        const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
+        store_split8(v, stp + off, stp + kABytes + off);
+      }
+      // B: 8 window positions of output bn per core row
+#pragma unroll
+      for (int q = tid; q < kTN * (kKC / 8); q += kProducerWarps * 32) {
+        const int bn = q % kTN, bq = q / kTN;
+        const float bkap = (float)(bn - kTN / 2);
+        const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float mp = (float)(m0 + bq * 8 + i) - halfW;
+          v[i] = ex2(fmaf(bt2, mp, btk));
+        }
+        const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
+        store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
+      }
+      // make the stores visible to the tensor core's async proxy, then arrive
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full[s]));
     }
-    issued = ch + 1;
   }
-  // all MMAs done: the last commit of each used stage
-  // (after a time-out the same bounded waits give in-flight MMAs a last chance to finish
-  // before the tensor memory is released)
-  bool ok_end = true;
-  if (issued >= 1)
-    ok_end = mbar_wait(smem_u32(&mbar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1, a.err);
-  if (issued >= 2)
-    ok_end = mbar_wait(smem_u32(&mbar[(issued - 2) & 1]), ((issued - 2) >> 1) & 1, a.err) && ok_end;
-  ok = __syncthreads_and(ok && ok_end);
+  // epilogue geometry: accumulator row = TMEM lane = 32 * (warp % 4) + lane; warps w and w + 4
+  // take the two halves of the TN columns, 8 at a time
+  const int lq = warp & 3, half = (warp >> 2) & 1;
+  const int rloc = 32 * lq + lane;
+  const int r_out = r0 + rloc;
+  // potential update: the marginals of this thread's outputs, loaded while the last MMAs run
+  float lm_pre[kTN / 2];
+#pragma unroll
+  for (int u = 0; u < kTN / 2; ++u) {
+    const int k = k0 + half * (kTN / 2) + u;
+    lm_pre[u] = (MODE == 1 && producer && r_out < a.n_rows && k <= k1)
+                    ? a.lmarg[(size_t)k * a.n_rows + r_out] : 0.f;
+  }
+  if (producer) ok = ok && mbar_wait(smem_u32(&done), 0, a.err);
+  ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  if (ok) {
-    // accumulator row = TMEM lane = 32 * (warp % 4) + lane; warps w and w + 4 take the two
-    // halves of the TN columns, 8 at a time
-    const int lq = warp & 3, ch = warp >> 2;
-    const int rloc = 32 * lq + lane;
-    const int r = r0 + rloc;
+  if (ok && producer) {
     const float al = s_alpha[rloc];
     const float mref = (float)s_lo[rloc] + halfW;
 #pragma unroll
     for (int cg = 0; cg < kTN / 2; cg += 8) {
-      const int n0 = ch * (kTN / 2) + cg;
+      const int n0 = half * (kTN / 2) + cg;
       uint32_t acc[8];
       const uint32_t taddr = tmem_d + ((uint32_t)(32 * lq) << 16) + (uint32_t)n0;
       asm volatile(
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
             "=r"(acc[6]), "=r"(acc[7])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (r < a.n_rows) {
+      if (r_out < a.n_rows) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int n = n0 + u;
@@ -354,21 +384,21 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
           float out = -INFINITY;
           if (al != -INFINITY) {
             if (cv > 0.f && isfinite(cv))
-              out = al + 2.f * kap * (mref - (float)kc) * c + log2f(cv);
+              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)kc), c, al), log2f(cv));
             else
               raise_error(a.err, FOT_ENONFINITE);
           }
-          const size_t yi = (size_t)k * a.n_rows + r;
+          const size_t yi = (size_t)k * a.n_rows + r_out;
           if (MODE == 0) {
             a.y[yi] = out;
           } else {
-            const float sv = out * kLn2;
-            const float lm = a.lmarg[yi];
+            const float sv = __fmul_rn(out, kLn2);
+            const float lm = lm_pre[cg + u];
             float pot;
             if (lm == -INFINITY) {
               pot = -INFINITY;
             } else {
-              pot = a.eps * (lm - sv);
+              pot = __fmul_rn(a.eps, __fsub_rn(lm, sv));
               if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
             }
             a.y[yi] = pot;
@@ -380,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 2) tc_pass_kernel(const __grid_const
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
+  if (warp == kProducerWarps)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(kTmemCols)
                  : "memory");
 }
@@ -471,11 +501,11 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw) {
   }
   ktimer_begin(s, kKTensor);
   if (tw == 64)
-    tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreads, TcShape<64>::kSmemBytes, s>>>(t);
+    tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreadsTC, TcShape<64>::kSmemBytes, s>>>(t);
   else if (tw == 32)
-    tc_pass_kernel<MODE, 32, MAXP><<<t.ctas, kThreads, TcShape<32>::kSmemBytes, s>>>(t);
+    tc_pass_kernel<MODE, 32, MAXP><<<t.ctas, kThreadsTC, TcShape<32>::kSmemBytes, s>>>(t);
   else
-    tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreads, TcShape<16>::kSmemBytes, s>>>(t);
+    tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreadsTC, TcShape<16>::kSmemBytes, s>>>(t);
   ktimer_end(s);
   return 2;
 }
