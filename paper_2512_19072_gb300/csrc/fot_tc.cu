@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   __shared__ uint64_t full[2], empty[2], done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ float s_alpha[kTM];
-  __shared__ int s_lo[kTM];
+  __shared__ int s_lo[kTM], s_wl[kTM];
   __shared__ int s_wmax;
   const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, (int)blockIdx.x)];
   if (error_latched(a.err)) return;
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
     }
     s_alpha[tid] = al;
     s_lo[tid] = lo;
+    s_wl[tid] = wl;
     atomicMax(&s_wmax, wl);
   }
   __syncthreads();
@@ -210,6 +211,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   const int ar = tid & (kTM - 1), ah = (tid >> 7) & 1;
   const float a_alpha = s_alpha[ar];
   const int a_lo = s_lo[ar];
+  // window positions m' >= the row's own window length hold only terms below 2^-kCut of every
+  // output of the tile (the provable window): their A values are written as zeros, with no
+  // load and no exponential (rows with short windows cost little in a long tile)
+  const int a_wl = s_wl[ar];
   const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
   // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
   // multiple of 32 and each chunk starts at a multiple of 64, so the float4 loads are
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   const bool vec_ok = (reinterpret_cast<uintptr_t>(xr) & 15u) == 0;
   float4 xq[8];
   auto load_x = [&](int m0) {
+    if (m0 + ah * 32 >= a_wl) return;                   // outside the row's window
     const int mb = a_lo + m0 + ah * 32;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -310,17 +316,27 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
       if (ch + 1 < nchunk) load_x(m0 + kKC);
       // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
       const float dbase = (float)(kc - (a_lo + m0 + ah * 32));
+      if (!a_live || m0 + ah * 32 >= a_wl) {
+        // no term of this row here: zeros
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        float v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float d = dbase - (float)(g * 8 + i);
-          v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - (a_live ? a_alpha : 0.f));   // -inf -> 0
+        for (int g = 0; g < 4; ++g) {
+          const uint32_t off = (uint32_t)((ar >> 3) * 1024 + (ah * 4 + g) * 128 + (ar & 7) * 16);
+          *reinterpret_cast<uint4*>(stp + off) = make_uint4(0u, 0u, 0u, 0u);
+          *reinterpret_cast<uint4*>(stp + kABytes + off) = make_uint4(0u, 0u, 0u, 0u);
         }
-        const int kg = ah * 4 + g;                        // core-matrix column in the stage
-        const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
-        store_split8(v, stp + off, stp + kABytes + off);
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float d = dbase - (float)(g * 8 + i);
+            v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - a_alpha);   // x = -inf -> 0
+          }
+          const int kg = ah * 4 + g;                      // core-matrix column in the stage
+          const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
+          store_split8(v, stp + off, stp + kABytes + off);
+        }
       }
       // B: 8 window positions of output bn per core row
 #pragma unroll
