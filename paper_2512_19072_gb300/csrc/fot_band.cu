@@ -41,10 +41,10 @@ namespace fot {
 //   a. alpha: with d0 = kc - 32 j, e(32 j + u, kc) = z[32 j + u] + t u - c d0^2, t = 2 c d0,
 //      so the maximum of chunk j at any centre is the support function of the upper convex
 //      hull of the points (u, z[32 j + u]) at slope t.  One thread per chunk builds that hull
-//      (monotone chain, at most 32 vertices) and the slopes of its edges, which decrease; the
-//      optimal vertex is the first edge with slope <= -t.  A warp takes a block of consecutive
-//      tiles; as kc grows so does t, so each lane walks its chunk's vertex pointer forward;
-//      a warp argmax gives alpha (the maximum at kc up to rounding) and its index.
+//      (monotone chain, at most 32 vertices) and the slopes of its edges, which decrease; a
+//      query is a binary search for the first edge slope <= -t.  A warp takes one tile at a
+//      time, lanes query their chunks, and a warp argmax gives alpha (the maximum at kc up to
+//      rounding) and its index.
 //   b. the window of step 2 above: the first and the last 32-wide chunk whose bound over the
 //      tile reaches LB - kCut (one ballot per 32 chunks).
 constexpr int kPlanThreads = 128;
@@ -124,32 +124,27 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
   const int nwords = (nch + 31) / 32;
-  // each warp a contiguous block of tiles: the optimal hull vertex of a chunk moves right as
-  // kc grows (the slope t does), so each lane walks its pointers forward
-  const int per = (T + kPlanThreads / 32 - 1) / (kPlanThreads / 32);
-  const int t_begin = warp * per, t_end = min(T, t_begin + per);
-  constexpr int kMaxWords = 4096 / kCW / 32;
-  int vp[kMaxWords];
-#pragma unroll
-  for (int w = 0; w < kMaxWords; ++w) vp[w] = 0;
-  for (int t = t_begin; t < t_end; ++t) {
+  for (int t = warp; t < T; t += kPlanThreads / 32) {
     const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
     // a. the maximum at kc: each lane its chunks, then a warp argmax
     float best = -INFINITY;
     int arg = 0x7fffffff;
-#pragma unroll
-    for (int w = 0; w < kMaxWords; ++w) {
-      if (w >= nwords) break;                             // warp-uniform
+    for (int w = 0; w < nwords; ++w) {
       const int j = 32 * w + lane;
       const int n = j < nch ? s_hn[j] : 0;
       if (n > 0) {
         const float d0 = (float)(kc - j * kCW);
         const float t2 = 2.f * c * d0;
         const float* hs = &s_hs[j * kHullS];
-        int p = vp[w];                                    // first edge with slope <= -t2
-        while (p < n - 1 && hs[p] > -t2) ++p;
-        vp[w] = p;
-        const int u = s_hu[j * kHullU + p];
+        int lo = 0, hi = n - 1;                           // first edge with slope <= -t2
+        while (lo < hi) {
+          const int md = (lo + hi) >> 1;
+          if (hs[md] <= -t2)
+            hi = md;
+          else
+            lo = md + 1;
+        }
+        const int u = s_hu[j * kHullU + lo];
         const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
         if (v > best) {
           best = v;
