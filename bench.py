@@ -177,6 +177,13 @@ FFMA_FLOP_PER_CLK_PER_SM = 256
 N_SM = 152
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel, from an ncu
+# capture of the current build on the benchmark workload (the capture and its command are in the
+# named profiles/ summary).  Keyed by (kernel, n, precision); a kernel that changes since its
+# capture must lose its entry (the bench line then reports traffic null).
+NCU_TRAFFIC = {}
+
+
 def _roofline(n, a, ktimes, work, loop_ms):
     """Roofline of the dominant kernel (largest device time in the event-timed loops): its
     algorithmic work over the CUDA-event time of its own launches, against the unit that
@@ -223,7 +230,10 @@ def _roofline(n, a, ktimes, work, loop_ms):
         roof = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peak, "unit": "GB/s",
                 "work": "x read once + 3 plan words per (row, tile) written",
                 "peak_source": "STREAM copy, " + peak_src}
-    roof.update({"kernel": dom, "frac": roof["achieved"] / roof["peak"], "traffic": None,
+    tr = NCU_TRAFFIC.get((dom, n, a.precision))
+    roof.update({"kernel": dom, "frac": roof["achieved"] / roof["peak"],
+                 "traffic": tr["bytes"] if tr else None,
+                 "traffic_source": tr["source"] if tr else None,
                  "launches": n_launch, "avg_launch_us": t_ms * 1e3 / max(n_launch, 1),
                  "kernels": kernels, "loop_ms": loop_ms,
                  "dense_equivalent_tflops": 2.0 * 4.0 * a.iters * n ** 3 / (loop_ms * 1e-3) / 1e12,
