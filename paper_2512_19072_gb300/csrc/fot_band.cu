@@ -5,7 +5,7 @@
 //
 // Work unit: one warp, 16 input rows r x one tile of 16 consecutive outputs o = k0 + i; lane
 // (h, i) = (lane / 16, lane % 16) owns rows 8h .. 8h+7 and output i.  Steps 1-2 run in
-// band_plan_kernel and leave (alpha, lo, window length) per (row, tile);
+// band_plan_kernel (one CTA per row) and leave (alpha, lo, window length) per (row, tile);
 // steps 3-4 run in band_pass_kernel.
 //
 // 1. Offset at every tile centre kc = k0 + 8: alpha_r = max_m e_r(m, kc) (up to rounding),
@@ -35,18 +35,18 @@
 namespace fot {
 
 // Per (row, tile) plan (tiles of tile_w = 16, 32 or 64 outputs): centre offset alpha, window
-// start lo and length wl.  One CTA of four warps plans one, two or four rows (a group of whole
-// warps per row, enough rows that one thread per tile fills the CTA).  The row is staged in shared memory
+// start lo and length wl.  One CTA of four warps per row.  The row is staged in shared memory
 // as z[m] = x[m] * scale - u^2 c (u = m mod 32, one pad word per 32-wide chunk), with the
 // chunk maxima of x * scale.
 //   a. alpha: with d0 = kc - 32 j, e(32 j + u, kc) = z[32 j + u] + t u - c d0^2, t = 2 c d0,
 //      so the maximum of chunk j at any centre is the support function of the upper convex
 //      hull of the points (u, z[32 j + u]) at slope t.  One thread per chunk builds that hull
 //      (monotone chain, at most 32 vertices) and the slopes of its edges, which decrease; a
-//      query is a binary search for the first edge slope <= -t.  One thread per tile queries
-//      the chunks in turn (the one holding kc first), skipping every chunk whose bound
-//      (chunk maximum less the nearest squared distance times c) cannot beat the best so far;
-//      alpha is the maximum at kc up to rounding.
+//      query is a binary search for the first edge slope <= -t.  16-wide tiles (many per row):
+//      one thread per tile queries the chunks in turn (the one holding kc first), skipping
+//      every chunk whose bound (chunk maximum less the nearest squared distance times c)
+//      cannot beat the best so far.  Wider tiles (fewer per row): a warp per tile, lanes
+//      query their chunks, then a warp argmax.  alpha is the maximum at kc up to rounding.
 //   b. the window of step 2 above: the first and the last 32-wide chunk whose bound over the
 //      tile reaches LB - kCut.
 constexpr int kPlanThreads = 128;
@@ -61,149 +61,205 @@ __host__ __device__ inline size_t plan_smem_bytes(int n_chunks) {
 }
 
 template <int MAXP>
-__global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab,
-                                                                 int rows_per_cta, int smem_per_row) {
-  extern __shared__ __align__(16) float s_dyn[];
-  // rows_per_cta rows per CTA, one group of G = 128 / rows_per_cta threads (whole warps) each
-  const int G = kPlanThreads / rows_per_cta;
-  const int grp = threadIdx.x / G, gt = threadIdx.x % G, gwarp = gt >> 5, lane = threadIdx.x & 31;
-  const int gw = (int)blockIdx.x * rows_per_cta + grp;
-  // a group without a row (the grid's tail) or whose problem has latched an error idles, but
-  // still meets the CTA's barriers
-  const bool active = gw < tab.plans;
-  const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, active ? gw : 0)];
-  const bool work = active && !error_latched(a.err);
-  const int row = gw - a.plan_base;
+__global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+  extern __shared__ __align__(16) float s_plan[];
+  const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, (int)blockIdx.x)];
+  if (error_latched(a.err)) return;                       // CTA-uniform
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = (int)blockIdx.x - a.plan_base;
   const int T = a.n_tiles, len = a.len, nch = a.n_chunks, tw = a.tile_w;
   const float c = a.c, sc = a.x_scale;
-  const float* xr = a.x + (size_t)(work ? row : 0) * len;
-  float* s_z = s_dyn + (size_t)grp * (smem_per_row / 4);
+  const float* xr = a.x + (size_t)row * len;
+  float* s_z = s_plan;
   float* s_cm = s_z + nch * (kCW + 1);
   int* s_hn = reinterpret_cast<int*>(s_cm + nch);
   float* s_hs = reinterpret_cast<float*>(s_hn + nch);                          // [j][k] edge k slope
   unsigned char* s_hu = reinterpret_cast<unsigned char*>(s_hs + nch * kHullS);   // [j][k] vertex u
 
-  // stage: each warp of the group takes whole chunks, four at a time (lane = position)
-  if (work) {
-    const float uc = -(float)(lane * lane) * c;
-    for (int j0 = gwarp * 4; j0 < nch; j0 += (G / 32) * 4) {
-      float v[4];
+  // stage: each warp takes whole chunks, four at a time (lane = position in the chunk)
+  const float uc = -(float)(lane * lane) * c;
+  for (int j0 = warp * 4; j0 < nch; j0 += kPlanThreads / 8) {
+    float v[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int m = (j0 + q) * kCW + lane;
-        v[q] = (j0 + q < nch && m < len) ? __fmul_rn(xr[m], sc) : -INFINITY;
-      }
+    for (int q = 0; q < 4; ++q) {
+      const int m = (j0 + q) * kCW + lane;
+      v[q] = (j0 + q < nch && m < len) ? __fmul_rn(xr[m], sc) : -INFINITY;
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (j0 + q >= nch) break;                         // warp-uniform
-        s_z[(j0 + q) * (kCW + 1) + lane] = __fadd_rn(v[q], uc);   // no contraction: the same
-                                                                    // rounding in every instance
-        const float mx = warp_max(v[q]);
-        if (lane == 0) s_cm[j0 + q] = mx;
-      }
+    for (int q = 0; q < 4; ++q) {
+      if (j0 + q >= nch) break;                           // warp-uniform
+      s_z[(j0 + q) * (kCW + 1) + lane] = __fadd_rn(v[q], uc);   // no contraction: the same
+                                                                  // rounding in every instance
+      const float mx = warp_max(v[q]);
+      if (lane == 0) s_cm[j0 + q] = mx;
     }
   }
   __syncthreads();
   // upper hulls, one thread per chunk (the padded rows keep the threads on different banks);
   // the top two vertices of the stack live in registers
-  if (work) {
-    for (int j = gt; j < nch; j += G) {
-      const float* zs = &s_z[j * (kCW + 1)];
-      unsigned char* hu = &s_hu[j * kHullU];
-      float* hs = &s_hs[j * kHullS];
-      int n = 0;
-      int u0 = 0, u1 = 0;                                 // second and top vertex
-      float z0 = 0.f, z1 = 0.f;
-      for (int u = 0; u < kCW; ++u) {
-        const float zu = zs[u];
-        if (zu == -INFINITY) continue;
-        // pop while the top lies on or below the segment from the one below it to u
-        while (n >= 2 && (z1 - z0) * (float)(u - u0) <= (zu - z0) * (float)(u1 - u0)) {
-          --n;
-          u1 = u0;
-          z1 = z0;
-          if (n >= 2) {
-            u0 = hu[n - 2];
-            z0 = zs[u0];
-          }
+  for (int j = tid; j < nch; j += kPlanThreads) {
+    const float* zs = &s_z[j * (kCW + 1)];
+    unsigned char* hu = &s_hu[j * kHullU];
+    float* hs = &s_hs[j * kHullS];
+    int n = 0;
+    int u0 = 0, u1 = 0;                                   // second and top vertex
+    float z0 = 0.f, z1 = 0.f;
+    for (int u = 0; u < kCW; ++u) {
+      const float zu = zs[u];
+      if (zu == -INFINITY) continue;
+      // pop while the top lies on or below the segment from the one below it to u
+      while (n >= 2 && (z1 - z0) * (float)(u - u0) <= (zu - z0) * (float)(u1 - u0)) {
+        --n;
+        u1 = u0;
+        z1 = z0;
+        if (n >= 2) {
+          u0 = hu[n - 2];
+          z0 = zs[u0];
         }
-        hu[n++] = (unsigned char)u;
-        u0 = u1;
-        z0 = z1;
-        u1 = u;
-        z1 = zu;
       }
-      // edge slopes (they only steer the vertex search: the fast division is enough)
-      for (int k = 0; k + 1 < n; ++k)
-        hs[k] = __fdividef(zs[hu[k + 1]] - zs[hu[k]], (float)(hu[k + 1] - hu[k]));
-      s_hn[j] = n;
+      hu[n++] = (unsigned char)u;
+      u0 = u1;
+      z0 = z1;
+      u1 = u;
+      z1 = zu;
     }
+    // edge slopes (they only steer the vertex search: the fast division is enough)
+    for (int k = 0; k + 1 < n; ++k)
+      hs[k] = __fdividef(zs[hu[k + 1]] - zs[hu[k]], (float)(hu[k + 1] - hu[k]));
+    s_hn[j] = n;
   }
   __syncthreads();
-  if (!work) return;
 
   const size_t np = (size_t)a.n_rows * T;
   float* p_alpha = a.plan;
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
-  // one thread per tile: every chunk's maximum at the centre (hull search), skipping the
-  // chunks whose bound (chunk maximum less the nearest squared distance times c) cannot beat
-  // the running best, starting from the chunk that holds the centre
-  for (int t = gt; t < T; t += G) {
+  if (tw == kBT) {
+    // one thread per tile: every chunk's maximum at the centre (hull search), skipping the
+    // chunks whose bound (chunk maximum less the nearest squared distance times c) cannot beat
+    // the running best, starting from the chunk that holds the centre
+    for (int t = tid; t < T; t += kPlanThreads) {
+      const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
+      float best = -INFINITY;
+      int arg = 0x7fffffff;
+      const int jc = min(kc, len - 1) / kCW;
+      for (int q = -1; q < nch; ++q) {
+        const int j = q < 0 ? jc : q;
+        if (q == jc) continue;                              // done first
+        const int n = s_hn[j];
+        if (n == 0) continue;
+        const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
+        const int dd = clo > kc ? clo - kc : (chi < kc ? kc - chi : 0);
+        if (!(fmaf(-(float)dd * (float)dd, c, s_cm[j]) > best)) continue;
+        const float d0 = (float)(kc - clo);
+        const float t2 = 2.f * c * d0;
+        const float* hs = &s_hs[j * kHullS];
+        int lo = 0, hi = n - 1;                             // first edge with slope <= -t2
+        while (lo < hi) {
+          const int md = (lo + hi) >> 1;
+          if (hs[md] <= -t2)
+            hi = md;
+          else
+            lo = md + 1;
+        }
+        const int u = s_hu[j * kHullU + lo];
+        const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
+        if (v > best || (v == best && clo + u < arg)) {
+          best = v;
+          arg = clo + u;
+        }
+      }
+      const size_t pi = (size_t)row * T + t;
+      if (best == -INFINITY) {                              // no finite term: empty row
+        p_alpha[pi] = -INFINITY;
+        p_lo[pi] = 0;
+        p_wl[pi] = 0;
+        continue;
+      }
+      // b. window: lower bound over the tile from the argmax term at the worse tile end, then
+      // the first and the last chunk whose bound over the tile reaches lb - kCut
+      const float dM = (float)(arg - kc);
+      const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
+      const float lb = best + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
+      int wlo = -1, whi = -1;
+      for (int j = 0; j < nch; ++j) {
+        const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
+        const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
+        if (fmaf(-(float)d * (float)d, c, s_cm[j]) >= lb - kCut) {
+          if (wlo < 0) wlo = j;
+          whi = j;
+        }
+      }
+      p_alpha[pi] = best;
+      p_lo[pi] = wlo * kCW;
+      p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
+    }
+
+    return;
+  }
+  // wider tiles (fewer per row): a warp per tile, lanes over chunks, then a warp argmax
+  const int nwords = (nch + 31) / 32;
+  for (int t = warp; t < T; t += kPlanThreads / 32) {
     const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
+    // a. the maximum at kc: each lane its chunks, then a warp argmax
     float best = -INFINITY;
     int arg = 0x7fffffff;
-    const int jc = min(kc, len - 1) / kCW;
-    for (int q = -1; q < nch; ++q) {
-      const int j = q < 0 ? jc : q;
-      if (q == jc) continue;                              // done first
-      const int n = s_hn[j];
-      if (n == 0) continue;
-      const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
-      const int dd = clo > kc ? clo - kc : (chi < kc ? kc - chi : 0);
-      if (!(fmaf(-(float)dd * (float)dd, c, s_cm[j]) > best)) continue;
-      const float d0 = (float)(kc - clo);
-      const float t2 = 2.f * c * d0;
-      const float* hs = &s_hs[j * kHullS];
-      int lo = 0, hi = n - 1;                             // first edge with slope <= -t2
-      while (lo < hi) {
-        const int md = (lo + hi) >> 1;
-        if (hs[md] <= -t2)
-          hi = md;
-        else
-          lo = md + 1;
-      }
-      const int u = s_hu[j * kHullU + lo];
-      const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
-      if (v > best || (v == best && clo + u < arg)) {
-        best = v;
-        arg = clo + u;
+    for (int w = 0; w < nwords; ++w) {
+      const int j = 32 * w + lane;
+      const int n = j < nch ? s_hn[j] : 0;
+      if (n > 0) {
+        const float d0 = (float)(kc - j * kCW);
+        const float t2 = 2.f * c * d0;
+        const float* hs = &s_hs[j * kHullS];
+        int lo = 0, hi = n - 1;                           // first edge with slope <= -t2
+        while (lo < hi) {
+          const int md = (lo + hi) >> 1;
+          if (hs[md] <= -t2)
+            hi = md;
+          else
+            lo = md + 1;
+        }
+        const int u = s_hu[j * kHullU + lo];
+        const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
+        if (v > best) {
+          best = v;
+          arg = j * kCW + u;
+        }
       }
     }
+    warp_argmax(best, arg);
     const size_t pi = (size_t)row * T + t;
     if (best == -INFINITY) {                              // no finite term: empty row
-      p_alpha[pi] = -INFINITY;
-      p_lo[pi] = 0;
-      p_wl[pi] = 0;
+      if (lane == 0) {
+        p_alpha[pi] = -INFINITY;
+        p_lo[pi] = 0;
+        p_wl[pi] = 0;
+      }
       continue;
     }
+    const float al = best;
     // b. window: lower bound over the tile from the argmax term at the worse tile end, then
     // the first and the last chunk whose bound over the tile reaches lb - kCut
     const float dM = (float)(arg - kc);
     const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
-    const float lb = best + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
+    const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
     int wlo = -1, whi = -1;
-    for (int j = 0; j < nch; ++j) {
+    for (int w = 0; w < nwords; ++w) {
+      const int j = 32 * w + lane;
       const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
       const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
-      if (fmaf(-(float)d * (float)d, c, s_cm[j]) >= lb - kCut) {
-        if (wlo < 0) wlo = j;
-        whi = j;
+      const float cmj = j < nch ? s_cm[j] : -INFINITY;
+      const unsigned bal = __ballot_sync(0xffffffffu, fmaf(-(float)d * (float)d, c, cmj) >= lb - kCut);
+      if (bal) {
+        if (wlo < 0) wlo = 32 * w + __ffs(bal) - 1;
+        whi = 32 * w + 31 - __clz(bal);
       }
     }
-    p_alpha[pi] = best;
-    p_lo[pi] = wlo * kCW;
-    p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
+    if (lane == 0) {
+      p_alpha[pi] = al;
+      p_lo[pi] = wlo * kCW;
+      p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
+    }
   }
 }
 
@@ -251,19 +307,10 @@ void band_table_finish(BandTable<MAXP>& t) {
 
 template <int MAXP>
 void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
-  // rows per CTA: enough that one thread per tile fills the CTA (1, 2 or 4), within the
-  // default 48 KB of dynamic shared memory
-  size_t per_row = 0;
-  int max_tiles = 1;
-  for (int q = 0; q < t.n; ++q) {
-    per_row = std::max(per_row, plan_smem_bytes(t.p[q].n_chunks));
-    max_tiles = std::max(max_tiles, t.p[q].n_tiles);
-  }
-  per_row = (per_row + 15) & ~(size_t)15;
-  int rows = kPlanThreads / std::min(kPlanThreads, ((max_tiles + 31) / 32) * 32);
-  while (rows > 1 && rows * per_row > 48 * 1024) rows /= 2;
+  size_t smem = 0;
+  for (int q = 0; q < t.n; ++q) smem = std::max(smem, plan_smem_bytes(t.p[q].n_chunks));
   ktimer_begin(s, kKPlan);
-  band_plan_kernel<MAXP><<<(t.plans + rows - 1) / rows, kPlanThreads, rows * per_row, s>>>(t, rows, (int)per_row);
+  band_plan_kernel<MAXP><<<t.plans, kPlanThreads, smem, s>>>(t);
   ktimer_end(s);
 }
 
