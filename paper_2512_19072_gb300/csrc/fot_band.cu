@@ -63,7 +63,6 @@ __host__ __device__ inline size_t plan_smem_bytes(int n_chunks) {
 template <int MAXP>
 __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   extern __shared__ __align__(16) float s_plan[];
-  pdl_enter();
   const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, (int)blockIdx.x)];
   if (error_latched(a.err)) return;                       // CTA-uniform
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -271,7 +270,6 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
 
 template <int MODE, int MAXP>
 __global__ void __launch_bounds__(kBW * 32, FOT_BAND_MIN_BLOCKS) band_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
-  pdl_enter();
   __shared__ __align__(16) float sA[kBW][2 * kSA];
   const int warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * kBW + warp;
@@ -312,14 +310,14 @@ void band_prepare(cudaStream_t s, const BandTable<MAXP>& t) {
   size_t smem = 0;
   for (int q = 0; q < t.n; ++q) smem = std::max(smem, plan_smem_bytes(t.p[q].n_chunks));
   ktimer_begin(s, kKPlan);
-  launch_pdl(band_plan_kernel<MAXP>, dim3(t.plans), dim3(kPlanThreads), smem, s, t);
+  band_plan_kernel<MAXP><<<t.plans, kPlanThreads, smem, s>>>(t);
   ktimer_end(s);
 }
 
 template <int MODE, int MAXP>
 void band_simt(cudaStream_t s, const BandTable<MAXP>& t) {
   ktimer_begin(s, kKBand);
-  launch_pdl(band_pass_kernel<MODE, MAXP>, dim3((t.items + kBW - 1) / kBW), dim3(kBW * 32), 0, s, t);
+  band_pass_kernel<MODE, MAXP><<<(t.items + kBW - 1) / kBW, kBW * 32, 0, s>>>(t);
   ktimer_end(s);
 }
 

@@ -22,35 +22,6 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// Programmatic dependent launch for the kernels of the Sinkhorn loop: on entry a kernel lets
-// the next one in the stream be scheduled (its CTAs then wait here, so the launch gap overlaps
-// this kernel's tail), then waits until the previous kernel has completed and its writes are
-// visible.  Outside such a launch both instructions do nothing.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-// Launch a loop kernel with programmatic stream serialization (a plain launch while the stream
-// is being captured into a graph).
-template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args&&... args) {
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = cap == cudaStreamCaptureStatusNone ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
-}
-
 // Latch the first device-side error of a context (later errors are dropped).
 __device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
 

@@ -147,7 +147,6 @@ __device__ __noinline__ void tc_declined_tile(const BandArgs& a, int rw, int til
 
 template <int MODE, int TN, int MAXP>
 __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
-  pdl_enter();
   constexpr int kTN = TN;
   constexpr int kStageBytes = TcShape<TN>::kStageBytes;
   constexpr int kBBytes = TcShape<TN>::kBBytes;
@@ -518,11 +517,11 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw) {
   }
   ktimer_begin(s, kKTensor);
   if (tw == 64)
-    launch_pdl(tc_pass_kernel<MODE, 64, MAXP>, dim3(t.ctas), dim3(kThreadsTC), TcShape<64>::kSmemBytes, s, t);
+    tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreadsTC, TcShape<64>::kSmemBytes, s>>>(t);
   else if (tw == 32)
-    launch_pdl(tc_pass_kernel<MODE, 32, MAXP>, dim3(t.ctas), dim3(kThreadsTC), TcShape<32>::kSmemBytes, s, t);
+    tc_pass_kernel<MODE, 32, MAXP><<<t.ctas, kThreadsTC, TcShape<32>::kSmemBytes, s>>>(t);
   else
-    launch_pdl(tc_pass_kernel<MODE, 16, MAXP>, dim3(t.ctas), dim3(kThreadsTC), TcShape<16>::kSmemBytes, s, t);
+    tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreadsTC, TcShape<16>::kSmemBytes, s>>>(t);
   ktimer_end(s);
   return 2;
 }
