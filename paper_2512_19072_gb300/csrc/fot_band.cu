@@ -42,11 +42,11 @@ namespace fot {
 //      so the maximum of chunk j at any centre is the support function of the upper convex
 //      hull of the points (u, z[32 j + u]) at slope t.  One thread per chunk builds that hull
 //      (monotone chain, at most 32 vertices) and the slopes of its edges, which decrease; a
-//      query is a binary search for the first edge slope <= -t.  16-wide tiles (many per row):
-//      one thread per tile queries the chunks in turn (the one holding kc first), skipping
-//      every chunk whose bound (chunk maximum less the nearest squared distance times c)
-//      cannot beat the best so far.  Wider tiles (fewer per row): a warp per tile, lanes
-//      query their chunks, then a warp argmax.  alpha is the maximum at kc up to rounding.
+//      query is a binary search for the first edge slope <= -t.  S threads per tile (S * T
+//      about the CTA's 128 threads) share its chunks, each skipping every chunk whose bound
+//      (chunk maximum less the nearest squared distance times c) cannot beat its best so far,
+//      all starting from the chunk that holds kc; a shuffle reduction gives alpha (the maximum
+//      at kc up to rounding) and its index.
 //   b. the window of step 2 above: the first and the last 32-wide chunk whose bound over the
 //      tile reaches LB - kCut.
 constexpr int kPlanThreads = 128;
@@ -134,131 +134,92 @@ __global__ void __launch_bounds__(kPlanThreads) band_plan_kernel(const __grid_co
   float* p_alpha = a.plan;
   int* p_lo = reinterpret_cast<int*>(a.plan + np);
   int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
-  if (tw == kBT) {
-    // one thread per tile: every chunk's maximum at the centre (hull search), skipping the
-    // chunks whose bound (chunk maximum less the nearest squared distance times c) cannot beat
-    // the running best, starting from the chunk that holds the centre
-    for (int t = tid; t < T; t += kPlanThreads) {
-      const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
-      float best = -INFINITY;
-      int arg = 0x7fffffff;
+  // S threads per tile (S a power of two, S * T about the CTA's 128 threads, within a warp):
+  // the S threads of a tile take its chunks in turn (every S-th), each skipping the chunks whose
+  // bound (chunk maximum less the nearest squared distance times c) cannot beat its best so
+  // far, all starting from the chunk that holds the centre; a shuffle reduction then gives the
+  // tile's maximum (leftmost index on ties) and its window
+  int S = 1;
+  while (S < 32 && 2 * S * T <= kPlanThreads) S *= 2;
+  const int per_pass = kPlanThreads / S;
+  const int slot = tid / S, sub = tid % S;
+  for (int base = 0; base < T; base += per_pass) {       // uniform across the CTA
+    const int t = base + slot;
+    const bool live = t < T;
+    const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
+    float best = -INFINITY;
+    int arg = 0x7fffffff;
+    auto query = [&](int j) {
+      const int n = s_hn[j];
+      if (n == 0) return;
+      const int clo = j * kCW;
+      const float d0 = (float)(kc - clo);
+      const float t2 = 2.f * c * d0;
+      const float* hs = &s_hs[j * kHullS];
+      int lo = 0, hi = n - 1;                             // first edge with slope <= -t2
+      while (lo < hi) {
+        const int md = (lo + hi) >> 1;
+        if (hs[md] <= -t2)
+          hi = md;
+        else
+          lo = md + 1;
+      }
+      const int u = s_hu[j * kHullU + lo];
+      const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
+      if (v > best || (v == best && clo + u < arg)) {
+        best = v;
+        arg = clo + u;
+      }
+    };
+    if (live) {
       const int jc = min(kc, len - 1) / kCW;
-      for (int q = -1; q < nch; ++q) {
-        const int j = q < 0 ? jc : q;
-        if (q == jc) continue;                              // done first
-        const int n = s_hn[j];
-        if (n == 0) continue;
+      query(jc);
+      for (int j = sub; j < nch; j += S) {
+        if (j == jc) continue;
         const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
         const int dd = clo > kc ? clo - kc : (chi < kc ? kc - chi : 0);
-        if (!(fmaf(-(float)dd * (float)dd, c, s_cm[j]) > best)) continue;
-        const float d0 = (float)(kc - clo);
-        const float t2 = 2.f * c * d0;
-        const float* hs = &s_hs[j * kHullS];
-        int lo = 0, hi = n - 1;                             // first edge with slope <= -t2
-        while (lo < hi) {
-          const int md = (lo + hi) >> 1;
-          if (hs[md] <= -t2)
-            hi = md;
-          else
-            lo = md + 1;
-        }
-        const int u = s_hu[j * kHullU + lo];
-        const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
-        if (v > best || (v == best && clo + u < arg)) {
-          best = v;
-          arg = clo + u;
-        }
+        if (fmaf(-(float)dd * (float)dd, c, s_cm[j]) > best) query(j);
       }
-      const size_t pi = (size_t)row * T + t;
-      if (best == -INFINITY) {                              // no finite term: empty row
-        p_alpha[pi] = -INFINITY;
-        p_lo[pi] = 0;
-        p_wl[pi] = 0;
-        continue;
+    }
+    for (int off = S / 2; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oa = __shfl_xor_sync(0xffffffffu, arg, off);
+      if (ob > best || (ob == best && oa < arg)) {
+        best = ob;
+        arg = oa;
       }
-      // b. window: lower bound over the tile from the argmax term at the worse tile end, then
-      // the first and the last chunk whose bound over the tile reaches lb - kCut
+    }
+    // b. window: lower bound over the tile from the argmax term at the worse tile end, then
+    // the first and the last chunk whose bound over the tile reaches lb - kCut
+    int wlo = 0x7fffffff, whi = -1;
+    if (live && best != -INFINITY) {
       const float dM = (float)(arg - kc);
       const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
       const float lb = best + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
-      int wlo = -1, whi = -1;
-      for (int j = 0; j < nch; ++j) {
+      for (int j = sub; j < nch; j += S) {
         const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
         const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
         if (fmaf(-(float)d * (float)d, c, s_cm[j]) >= lb - kCut) {
-          if (wlo < 0) wlo = j;
+          wlo = min(wlo, j);
           whi = j;
         }
       }
-      p_alpha[pi] = best;
-      p_lo[pi] = wlo * kCW;
-      p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
     }
-
-    return;
-  }
-  // wider tiles (fewer per row): a warp per tile, lanes over chunks, then a warp argmax
-  const int nwords = (nch + 31) / 32;
-  for (int t = warp; t < T; t += kPlanThreads / 32) {
-    const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
-    // a. the maximum at kc: each lane its chunks, then a warp argmax
-    float best = -INFINITY;
-    int arg = 0x7fffffff;
-    for (int w = 0; w < nwords; ++w) {
-      const int j = 32 * w + lane;
-      const int n = j < nch ? s_hn[j] : 0;
-      if (n > 0) {
-        const float d0 = (float)(kc - j * kCW);
-        const float t2 = 2.f * c * d0;
-        const float* hs = &s_hs[j * kHullS];
-        int lo = 0, hi = n - 1;                           // first edge with slope <= -t2
-        while (lo < hi) {
-          const int md = (lo + hi) >> 1;
-          if (hs[md] <= -t2)
-            hi = md;
-          else
-            lo = md + 1;
-        }
-        const int u = s_hu[j * kHullU + lo];
-        const float v = fmaf(-d0 * d0, c, fmaf((float)u, t2, s_z[j * (kCW + 1) + u]));
-        if (v > best) {
-          best = v;
-          arg = j * kCW + u;
-        }
-      }
+    for (int off = S / 2; off > 0; off >>= 1) {
+      wlo = min(wlo, __shfl_xor_sync(0xffffffffu, wlo, off));
+      whi = max(whi, __shfl_xor_sync(0xffffffffu, whi, off));
     }
-    warp_argmax(best, arg);
-    const size_t pi = (size_t)row * T + t;
-    if (best == -INFINITY) {                              // no finite term: empty row
-      if (lane == 0) {
+    if (live && sub == 0) {
+      const size_t pi = (size_t)row * T + t;
+      if (best == -INFINITY) {                            // no finite term: empty row
         p_alpha[pi] = -INFINITY;
         p_lo[pi] = 0;
         p_wl[pi] = 0;
+      } else {
+        p_alpha[pi] = best;
+        p_lo[pi] = wlo * kCW;
+        p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
       }
-      continue;
-    }
-    const float al = best;
-    // b. window: lower bound over the tile from the argmax term at the worse tile end, then
-    // the first and the last chunk whose bound over the tile reaches lb - kCut
-    const float dM = (float)(arg - kc);
-    const float ka = (float)(k0 - kc), kb = (float)(k1 - kc);
-    const float lb = al + fminf(fmaf(2.f * ka, dM * c, -ka * ka * c), fmaf(2.f * kb, dM * c, -kb * kb * c));
-    int wlo = -1, whi = -1;
-    for (int w = 0; w < nwords; ++w) {
-      const int j = 32 * w + lane;
-      const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
-      const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
-      const float cmj = j < nch ? s_cm[j] : -INFINITY;
-      const unsigned bal = __ballot_sync(0xffffffffu, fmaf(-(float)d * (float)d, c, cmj) >= lb - kCut);
-      if (bal) {
-        if (wlo < 0) wlo = 32 * w + __ffs(bal) - 1;
-        whi = 32 * w + 31 - __clz(bal);
-      }
-    }
-    if (lane == 0) {
-      p_alpha[pi] = al;
-      p_lo[pi] = wlo * kCW;
-      p_wl[pi] = min((whi + 1) * kCW, len) - wlo * kCW;
     }
   }
 }
