@@ -122,6 +122,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
     }
     const float halfW = 0.5f * (float)W;
     const float t2 = 2.f * kap * c, tk = -kap * kap * c;
+    const float rstep = ex2(t2);                          // B[m' + 1] / B[m']
     for (int m0 = 0; m0 < W; m0 += 32) {
 #pragma unroll
       for (int rr = 0; rr < kBR; ++rr) {
@@ -142,9 +143,11 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
       float mp = (float)m0 - halfW;
 #pragma unroll 2
       for (int j = 0; j < 32; j += 4) {
+        // B at four consecutive positions: one exponential, then the constant ratio 2^t2
         float b[4];
+        b[0] = ex2(fmaf(t2, mp, tk));
 #pragma unroll
-        for (int u = 0; u < 4; ++u) b[u] = ex2(fmaf(t2, mp + (float)u, tk));
+        for (int u = 1; u < 4; ++u) b[u] = __fmul_rn(b[u - 1], rstep);
         mp += 4.f;
 #pragma unroll
         for (int rr = 0; rr < kBR; ++rr) {

@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
         const int bn = q % kTN, bq = q / kTN;
         const float bkap = (float)(bn - kTN / 2);
         const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
+        // eight consecutive positions: one exponential, then the constant ratio 2^bt2
         float v[8];
+        v[0] = ex2(fmaf(bt2, (float)(m0 + bq * 8) - halfW, btk));
+        const float rstep = ex2(bt2);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float mp = (float)(m0 + bq * 8 + i) - halfW;
-          v[i] = ex2(fmaf(bt2, mp, btk));
-        }
+        for (int i = 1; i < 8; ++i) v[i] = __fmul_rn(v[i - 1], rstep);
         const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
         store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
       }
