@@ -34,7 +34,7 @@ METRIC = "FOT Mpixel*iter/s at 1024^2 (mixed vs FP32, <=1e-4 marginal L1); % of 
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fot", choices=["fot", "reference"])
     p.add_argument("--precision", default="mixed", choices=["fp32", "fp32_dense", "mixed"])

@@ -22,6 +22,14 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+// log2(x) with the MUFU.LG2 unit (PTX lg2.approx.ftz.f32: absolute error about 2^-22 for
+// normal x; subnormal x flushes to zero and gives -inf).
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Latch the first device-side error of a context (later errors are dropped).
 __device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
 

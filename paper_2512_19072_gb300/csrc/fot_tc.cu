@@ -20,7 +20,8 @@
 //
 // Precision: each operand is split into two BF16 parts, v = hi + lo (hi = bf16(v),
 // lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
-// about 2^-16 relative per product instead of 2^-8, FP32 accumulation.
+// about 2^-16 relative per product instead of 2^-8, FP32 accumulation.  The epilogue takes
+// log2 of the accumulator with the MUFU unit (about 2^-22 absolute), far below that.
 //
 // A CTA uses the tensor cores only when the tilt bound holds for the common window length W
 // of its 128 rows: |kap| W c <= 48 with |kap| <= TN / 2.  Then every output's largest term has
@@ -154,11 +155,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t full[2], empty[2], done;
   __shared__ uint32_t tmem_base_sh;
-  __shared__ float s_alpha[kTM];
-  __shared__ int s_lo[kTM], s_wl[kTM];
-  __shared__ int s_wmax;
+  __shared__ int s_wm[kTM / 32], s_err;
   const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, (int)blockIdx.x)];
-  if (error_latched(a.err)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lb = (int)blockIdx.x - a.cta_base;
   const int blk = lb / a.n_tiles, tile = lb % a.n_tiles;
@@ -166,55 +164,27 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   const int k0 = tile * kTN, kc = k0 + kTN / 2;
   const int k1 = min(k0 + kTN, a.len) - 1;
   const float c = a.c, sc = a.x_scale;
-  const size_t np = (size_t)a.n_rows * a.n_tiles;
-  const float* __restrict__ p_alpha = a.plan;
-  const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
-  const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
-
-  // per-row plan and the common window length
-  if (tid == 0) s_wmax = 0;
-  __syncthreads();
-  if (tid < kTM) {
-    const int r = r0 + tid;
-    float al = -INFINITY;
-    int lo = 0, wl = 0;
-    if (r < a.n_rows) {
-      const size_t pi = (size_t)r * a.n_tiles + tile;
-      al = p_alpha[pi];
-      lo = p_lo[pi];
-      wl = p_wl[pi];
-    }
-    s_alpha[tid] = al;
-    s_lo[tid] = lo;
-    s_wl[tid] = wl;
-    atomicMax(&s_wmax, wl);
-  }
-  __syncthreads();
-  const int W = ((s_wmax + kKC - 1) / kKC) * kKC;
-  const float kmax = (float)(kTN / 2);
-  const bool take = s_wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
-  if (!take) {                                          // CTA-uniform
-    const int rw = r0 + warp * 2 * kBR;                 // producer warp w: rows rw .. rw + 15
-    if (warp < kProducerWarps && rw < a.n_rows)
-      tc_declined_tile<MODE, TN>(a, rw, tile, k0, reinterpret_cast<float*>(smem) + warp * 2 * kSA);
-    return;
-  }
-  if (tid == 0) atomicAdd(a.tc_terms, (unsigned long long)W * kTN * kTM);
-
-  const uint32_t sbase = smem_u32(smem);
-  const float halfW = 0.5f * (float)W;
-  const int nchunk = W / kKC;
   const bool producer = warp < kProducerWarps;
 
-  // producer roles: A row r = tid % 128, half h = tid / 128 (32 window positions each);
-  // B: core rows q = tid, tid + 256, ... of TN outputs x 8 groups of 8 positions
+  // producer roles: A row r0 + ar (ar = tid % 128, which is also the accumulator row, i.e.
+  // the tensor-memory lane 32 (warp % 4) + lane, that this thread reads in the epilogue),
+  // half ah = tid / 128 (32 window positions each); B: core rows q = tid, tid + 256, ... of
+  // TN outputs x 8 groups of 8 positions.  Both threads of a row read its plan entry straight
+  // from global memory and start the loads of its first window chunk before any barrier, so
+  // that the CTA waits out one memory latency before its first stage instead of three.
   const int ar = tid & (kTM - 1), ah = (tid >> 7) & 1;
-  const float a_alpha = s_alpha[ar];
-  const int a_lo = s_lo[ar];
+  float a_alpha = -INFINITY;
+  int a_lo = 0, a_wl = 0;
+  if (producer && r0 + ar < a.n_rows) {
+    const size_t np = (size_t)a.n_rows * a.n_tiles;
+    const size_t pi = (size_t)(r0 + ar) * a.n_tiles + tile;
+    a_alpha = a.plan[pi];
+    a_lo = reinterpret_cast<const int*>(a.plan + np)[pi];
+    a_wl = reinterpret_cast<const int*>(a.plan + 2 * np)[pi];
+  }
   // window positions m' >= the row's own window length hold only terms below 2^-kCut of every
   // output of the tile (the provable window): their A values are written as zeros, with no
   // load and no exponential (rows with short windows cost little in a long tile)
-  const int a_wl = s_wl[ar];
   const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
   // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
   // multiple of 32 and each chunk starts at a multiple of 64, so the float4 loads are
@@ -242,6 +212,13 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   };
   if (producer) load_x(0);                  // in flight while the CTA sets up
 
+  // the common window length of the 128 rows: warps 0-3 hold one thread per row
+  int wm = a_wl;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, off));
+  if (lane == 0 && warp < kTM / 32) s_wm[warp] = wm;
+  if (tid == 0) s_err = error_latched(a.err) ? 1 : 0;   // one read: the exit is CTA-uniform
+
   // the MMA warp owns the tensor memory (128 x TN FP32 accumulator) and the barriers:
   // full[s] (256 producer arrivals: stage s written), empty[s] (the commit of the MMAs that
   // read stage s), done (the commit after the last chunk)
@@ -261,6 +238,25 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int wmax = max(max(s_wm[0], s_wm[1]), max(s_wm[2], s_wm[3]));
+  const int W = ((wmax + kKC - 1) / kKC) * kKC;
+  const float kmax = (float)(kTN / 2);
+  const bool take = wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
+  if (s_err || !take) {                                 // CTA-uniform
+    if (warp == kProducerWarps)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base_sh),
+                   "r"(kTmemCols) : "memory");
+    if (s_err) return;
+    const int rw = r0 + warp * 2 * kBR;                 // producer warp w: rows rw .. rw + 15
+    if (warp < kProducerWarps && rw < a.n_rows)
+      tc_declined_tile<MODE, TN>(a, rw, tile, k0, reinterpret_cast<float*>(smem) + warp * 2 * kSA);
+    return;
+  }
+  if (tid == 0) atomicAdd(a.tc_terms, (unsigned long long)W * kTN * kTM);
+
+  const uint32_t sbase = smem_u32(smem);
+  const float halfW = 0.5f * (float)W;
+  const int nchunk = W / kKC;
   const uint32_t tmem_d = tmem_base_sh;
   bool ok = true;
 
@@ -376,8 +372,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (ok && producer) {
-    const float al = s_alpha[rloc];
-    const float mref = (float)s_lo[rloc] + halfW;
+    const float al = a_alpha;                       // rloc == ar: this thread's own row
+    const float mref = (float)a_lo + halfW;
 #pragma unroll
     for (int cg = 0; cg < kTN / 2; cg += 8) {
       const int n0 = half * (kTN / 2) + cg;
@@ -400,7 +396,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
           float out = -INFINITY;
           if (al != -INFINITY) {
             if (cv > 0.f && isfinite(cv))
-              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)kc), c, al), log2f(cv));
+              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)kc), c, al), lg2(cv));
             else
               raise_error(a.err, FOT_ENONFINITE);
           }
