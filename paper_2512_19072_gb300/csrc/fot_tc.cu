@@ -11,11 +11,11 @@
 // (one exponential per row and window position) between more outputs; the host picks the
 // widest one whose tilt bound the problem's eps allows.
 //
-// Warp roles: eight producer warps generate the operands of each 64-position stage in shared
+// Warp roles: eight producer warps generate the operands of each 32-position stage in shared
 // memory (canonical no-swizzle K-major layout) and arrive on the stage's "full" mbarrier; one
 // more warp owns the tensor memory and issues the stage's MMAs once all producers have
 // arrived, committing to the stage's "empty" mbarrier, which the producers wait on before
-// reusing it (two stages).  A last commit signals the epilogue, in which the producers read
+// reusing it (a ring of four stages).  A last commit signals the epilogue, in which the producers read
 // the accumulator (the potential-update pass prefetches its marginals during the last MMAs).
 //
 // Precision: each operand is split into two BF16 parts, v = hi + lo (hi = bf16(v),
@@ -42,19 +42,23 @@ namespace fot {
 namespace {
 
 constexpr int kTM = 128;            // rows per CTA (MMA M, TMEM lanes)
-constexpr int kKC = 64;             // window positions per pipeline stage
+constexpr int kKC = 32;             // window positions per pipeline stage
+constexpr int kStages = 4;          // operand stages in flight
+constexpr int kPH = kKC / 2;        // window positions per producer thread and stage
+constexpr int kGroupBytes = (kKC / 8) * 128;   // bytes between 8-row core-matrix groups
+constexpr int kRouteKC = 64;        // window rounding of the host's tile-width estimate
 constexpr int kProducerWarps = 8;   // operand producers (256 threads)
 constexpr int kThreadsTC = kProducerWarps * 32 + 32;   // + the MMA-issuing warp
 constexpr float kTiltMaxTC = 48.f;
 constexpr int kSpin = 1 << 20;      // bounded mbarrier polls
 
-// shared-memory layout of one stage (bytes): A_hi, A_lo (128 x 64 bf16 each), B_hi, B_lo
-// (TN x 64 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 1024 + kg * 128.
-constexpr int kABytes = kTM * kKC * 2;   // 16384
+// shared-memory layout of one stage (bytes): A_hi, A_lo (128 x 32 bf16 each), B_hi, B_lo
+// (TN x 32 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 512 + kg * 128.
+constexpr int kABytes = kTM * kKC * 2;   // 8192
 template <int TN> struct TcShape {
   static constexpr int kBBytes = TN * kKC * 2;
   static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-  static constexpr int kSmemBytes = 2 * kStageBytes + 1024;   // 2 stages + slack
+  static constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // the ring + slack
   static constexpr uint32_t kTmemCols = TN < 32 ? 32 : TN;    // power of two >= 32
 };
 
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   constexpr int kBBytes = TcShape<TN>::kBBytes;
   constexpr uint32_t kTmemCols = TcShape<TN>::kTmemCols;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full[2], empty[2], done;
+  __shared__ uint64_t full[kStages], empty[kStages], done;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int s_wm[kTM / 32], s_err;
   const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, (int)blockIdx.x)];
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
 
   // producer roles: A row r0 + ar (ar = tid % 128, which is also the accumulator row, i.e.
   // the tensor-memory lane 32 (warp % 4) + lane, that this thread reads in the epilogue),
-  // half ah = tid / 128 (32 window positions each); B: core rows q = tid, tid + 256, ... of
+  // half ah = tid / 128 (16 window positions each); B: core rows q = tid, tid + 256, ... of
   // TN outputs x 8 groups of 8 positions.  Both threads of a row read its plan entry straight
   // from global memory and start the loads of its first window chunk before any barrier, so
   // that the CTA waits out one memory latency before its first stage instead of three.
@@ -186,19 +190,19 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
   // output of the tile (the provable window): their A values are written as zeros, with no
   // load and no exponential (rows with short windows cost little in a long tile)
   const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
-  // x of the next chunk, prefetched: 32 consecutive window positions of row ar.  lo is a
-  // multiple of 32 and each chunk starts at a multiple of 64, so the float4 loads are
-  // aligned; positions at or beyond len read -inf (the kernel skips rows without mass).
+  // x of the next chunk, prefetched: 16 consecutive window positions of row ar.  lo and each
+  // chunk start are multiples of 32, so the float4 loads are aligned; positions at or
+  // beyond len read -inf (the kernel skips rows without mass).
   const bool a_live = producer && a_alpha != -INFINITY;
   // the 16-byte vector load needs the row base aligned too: x + row * len is 16-byte aligned
   // only when row * len is a multiple of 4 (window starts are multiples of 32)
   const bool vec_ok = (reinterpret_cast<uintptr_t>(xr) & 15u) == 0;
-  float4 xq[8];
+  float4 xq[kPH / 4];
   auto load_x = [&](int m0) {
-    if (m0 + ah * 32 >= a_wl) return;                   // outside the row's window
-    const int mb = a_lo + m0 + ah * 32;
+    if (m0 + ah * kPH >= a_wl) return;                  // outside the row's window
+    const int mb = a_lo + m0 + ah * kPH;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < kPH / 4; ++q) {
       const int m = mb + 4 * q;
       if (a_live && vec_ok && m + 3 < a.len) {
         xq[q] = __ldg(reinterpret_cast<const float4*>(xr + m));
@@ -227,10 +231,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
                  :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     if (lane == 0) {
-      mbar_init(smem_u32(&full[0]), kProducerWarps * 32);
-      mbar_init(smem_u32(&full[1]), kProducerWarps * 32);
-      mbar_init(smem_u32(&empty[0]), 1);
-      mbar_init(smem_u32(&empty[1]), 1);
+      for (int i = 0; i < kStages; ++i) {
+        mbar_init(smem_u32(&full[i]), kProducerWarps * 32);
+        mbar_init(smem_u32(&empty[i]), 1);
+      }
       mbar_init(smem_u32(&done), 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -265,8 +269,8 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
     if (lane == 0) {
       const uint32_t idesc = instr_desc(kTM, kTN);
       for (int ch = 0; ch < nchunk; ++ch) {
-        const int s = ch & 1;
-        if (!mbar_wait(smem_u32(&full[s]), (ch >> 1) & 1, a.err)) {
+        const int s = ch % kStages;
+        if (!mbar_wait(smem_u32(&full[s]), (ch / kStages) & 1, a.err)) {
           ok = false;
           break;
         }
@@ -275,10 +279,10 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
         const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
 #pragma unroll
         for (int ks = 0; ks < kKC / 16; ++ks) {
-          const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, 1024);
-          const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, 1024);
-          const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, 1024);
-          const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, 1024);
+          const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, kGroupBytes);
+          const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, kGroupBytes);
+          const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, kGroupBytes);
+          const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, kGroupBytes);
           mma_bf16(tmem_d, dAh, dBh, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
           mma_bf16(tmem_d, dAh, dBl, idesc, 1u);
           mma_bf16(tmem_d, dAl, dBh, idesc, 1u);
@@ -293,44 +297,44 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
     __syncwarp();
   } else {
     for (int ch = 0; ch < nchunk; ++ch) {
-      const int s = ch & 1;
-      // stage free again: the MMAs of chunk ch - 2 (its previous use) have completed
-      if (ch >= 2 && !mbar_wait(smem_u32(&empty[s]), ((ch - 2) >> 1) & 1, a.err)) {
+      const int s = ch % kStages;
+      // stage free again: the MMAs of chunk ch - kStages (its previous use) have completed
+      if (ch >= kStages && !mbar_wait(smem_u32(&empty[s]), ((ch - kStages) / kStages) & 1, a.err)) {
         ok = false;
         break;
       }
       unsigned char* const stp = smem + s * kStageBytes;
       const int m0 = ch * kKC;
-      float xv[32];
+      float xv[kPH];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int q = 0; q < kPH / 4; ++q) {
         xv[4 * q] = xq[q].x;
         xv[4 * q + 1] = xq[q].y;
         xv[4 * q + 2] = xq[q].z;
         xv[4 * q + 3] = xq[q].w;
       }
       if (ch + 1 < nchunk) load_x(m0 + kKC);
-      // A: 32 consecutive window positions of row ar -> 4 core-matrix rows of 8 values
-      const float dbase = (float)(kc - (a_lo + m0 + ah * 32));
-      if (!a_live || m0 + ah * 32 >= a_wl) {
+      // A: 16 consecutive window positions of row ar -> 2 core-matrix rows of 8 values
+      const float dbase = (float)(kc - (a_lo + m0 + ah * kPH));
+      if (!a_live || m0 + ah * kPH >= a_wl) {
         // no term of this row here: zeros
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const uint32_t off = (uint32_t)((ar >> 3) * 1024 + (ah * 4 + g) * 128 + (ar & 7) * 16);
+        for (int g = 0; g < kPH / 8; ++g) {
+          const uint32_t off = (uint32_t)((ar >> 3) * kGroupBytes + (ah * (kPH / 8) + g) * 128 + (ar & 7) * 16);
           *reinterpret_cast<uint4*>(stp + off) = make_uint4(0u, 0u, 0u, 0u);
           *reinterpret_cast<uint4*>(stp + kABytes + off) = make_uint4(0u, 0u, 0u, 0u);
         }
       } else {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < kPH / 8; ++g) {
           float v[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const float d = dbase - (float)(g * 8 + i);
             v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - a_alpha);   // x = -inf -> 0
           }
-          const int kg = ah * 4 + g;                      // core-matrix column in the stage
-          const uint32_t off = (uint32_t)((ar >> 3) * 1024 + kg * 128 + (ar & 7) * 16);
+          const int kg = ah * (kPH / 8) + g;              // core-matrix column in the stage
+          const uint32_t off = (uint32_t)((ar >> 3) * kGroupBytes + kg * 128 + (ar & 7) * 16);
           store_split8(v, stp + off, stp + kABytes + off);
         }
       }
@@ -346,7 +350,7 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
         const float rstep = ex2(bt2);
 #pragma unroll
         for (int i = 1; i < 8; ++i) v[i] = __fmul_rn(v[i - 1], rstep);
-        const uint32_t off = (uint32_t)((bn >> 3) * 1024 + bq * 128 + (bn & 7) * 16);
+        const uint32_t off = (uint32_t)((bn >> 3) * kGroupBytes + bq * 128 + (bn & 7) * 16);
         store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
       }
       // make the stores visible to the tensor core's async proxy, then arrive
@@ -490,14 +494,14 @@ int64_t tc_terms(fot_ctx* c) {
 // each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to whole
 // stages, since the hull of a tile's windows grows where the transport map jumps across
 // zero-mass gaps; else 16 when a 16-wide tile can meet the bound at all (a taken tile has
-// W >= kKC); else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
+// W >= kRouteKC); else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
 int tc_width_for(float c) {
   for (int tn = 64; tn >= 32; tn /= 2) {
     const float w = (float)tn + 2.f * sqrtf(kCut / c);
-    const float wr = 2.f * ceilf(w / (float)kKC) * (float)kKC;
+    const float wr = 2.f * ceilf(w / (float)kRouteKC) * (float)kRouteKC;
     if ((float)(tn / 2) * wr * c <= kTiltMaxTC && (float)(tn / 2) * (float)(tn / 2) * c <= 32.f) return tn;
   }
-  if ((float)(kBT / 2) * (float)kKC * c <= kTiltMaxTC) return 16;
+  if ((float)(kBT / 2) * (float)kRouteKC * c <= kTiltMaxTC) return 16;
   return 0;
 }
 
