@@ -303,6 +303,43 @@ def marginal_l1(f, psi, a, b, eps):
     return float(np.abs(row - a).sum() + np.abs(col - b).sum())
 
 
+def source_violation(f, psi, a, eps):
+    """||Gamma 1 - a||_1: the source half of the total variation of the marginal violation
+    (the convergence measure Sec. 2 names).  Right after a V-half the target half is zero up to
+    rounding (psi makes the column sums equal b), so it is the whole measure there."""
+    row, _ = plan_marginals(f, psi, eps)
+    return float(np.abs(row - a).sum())
+
+
+def fot_iterate_tol(g, G, eps, max_iters, tol, check_every):
+    """Algorithm 1's loop with a convergence stop (Sec. 2): after every check_every iterations
+    (and after the last allowed one) measure the marginal violation of the current iterate
+    (f_t, psi_t) at eps_t and stop at the first check where it is <= tol.
+
+    eps: scalar or max_iters per-iteration values.  Returns fot_iterate's dict plus "iters"
+    (iterations done) and "tv" (the last measured violation)."""
+    a, b = marginal(g), marginal(G)
+    la, lb = log0(a), log0(b)
+    eps_arr = np.atleast_1d(np.asarray(eps, dtype=np.float64))
+    if len(eps_arr) == 1:
+        eps_arr = np.full(max_iters, eps_arr[0])
+    n_r, n_c = a.shape
+    psi = np.full((n_r, n_c), eps_arr[0] * math.log(1.0 / (n_r * n_c)))
+    f = S = None
+    t, tv = 0, math.inf
+    while t < max_iters:
+        for _ in range(min(check_every, max_iters - t)):
+            e = float(eps_arr[t])
+            f, S = u_update(psi, la, e)
+            psi, _ = v_update(f, lb, e)
+            t += 1
+        tv = source_violation(f, psi, a, float(eps_arr[t - 1]))
+        if tv <= tol:
+            break
+    return {"f": f, "psi": psi, "S_last": S, "a": a, "b": b, "eps_last": float(eps_arr[t - 1]),
+            "iters": t, "tv": tv}
+
+
 def dual_objective(f, psi, a, b, eps):
     """D(f, psi) = <f, a> + <psi, b> - eps sum Gamma + eps (entropic dual; zero-mass pixels
     contribute 0 to the inner products)."""

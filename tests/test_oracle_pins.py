@@ -253,6 +253,57 @@ def test_marginal_l1_matches_dense_plan():
     assert abs(fot.dual_objective(r["f"], r["psi"], r["a"], r["b"], eps) - D) < 1e-12
 
 
+# P13: the convergence stop (Sec. 2).  The source violation against the row sums of the dense
+# plan Gamma = exp((f + psi - C)/eps) (the target half vanishing after a V-half), and the stop
+# against the violations of the dense plan at the checks before and at it.
+def _dense_violation(f, psi, a, b, eps):
+    n_r, n_c = f.shape
+    jj, kk = np.meshgrid(np.arange(n_r), np.arange(n_c), indexing="ij")
+    P = np.stack([jj.ravel(), kk.ravel()], 1).astype(float)
+    C = ((P[:, None] - P[None]) ** 2).sum(-1) / 2
+    Gam = np.exp((f.ravel()[:, None] + psi.ravel()[None, :] - C) / eps)
+    return np.abs(Gam.sum(1) - a.ravel()).sum(), np.abs(Gam.sum(0) - b.ravel()).sum()
+
+
+def test_p13_source_violation_matches_dense_plan():
+    rng = np.random.default_rng(17)
+    g, G = _rand_masses(rng, 6, 5, zero_frac=0.2)
+    g[0, 0] = 0.0
+    for eps, iters in ((0.8, 2), (2.5, 4)):
+        r = fot.fot_iterate(g, G, eps, iters)
+        src, tgt = _dense_violation(r["f"], r["psi"], r["a"], r["b"], eps)
+        assert tgt < 1e-13                      # the V-half left the column sums at b
+        assert src > 1e-4                       # not yet converged: the check is not vacuous
+        assert abs(fot.source_violation(r["f"], r["psi"], r["a"], eps) - src) < 1e-13
+
+
+def test_p13_stop_rule_against_dense_plan():
+    rng = np.random.default_rng(19)
+    g, G = _rand_masses(rng, 5, 6, zero_frac=0.15)
+    eps, k, max_iters = 1.2, 3, 30
+    # the violations of the dense plan at every check, by brute force
+    tvs = []
+    for t in range(k, max_iters + 1, k):
+        r = fot.fot_iterate(g, G, eps, t)
+        tvs.append(sum(_dense_violation(r["f"], r["psi"], r["a"], r["b"], eps)))
+    assert all(x > y for x, y in zip(tvs, tvs[1:]))          # decreasing here: a clean test
+    i = 3
+    tol = (tvs[i] * tvs[i - 1]) ** 0.5                       # between the checks i-1 and i
+    r = fot.fot_iterate_tol(g, G, eps, max_iters, tol, k)
+    assert r["iters"] == (i + 1) * k
+    assert abs(r["tv"] - tvs[i]) < 1e-12 and r["tv"] <= tol
+    ref = fot.fot_iterate(g, G, eps, (i + 1) * k)
+    assert np.array_equal(r["f"], ref["f"]) and np.array_equal(r["psi"], ref["psi"])
+    assert np.array_equal(r["S_last"], ref["S_last"])
+    # never below tol: every check runs, the last one at max_iters (not a multiple of k here)
+    r = fot.fot_iterate_tol(g, G, eps, 28, 0.0, k)
+    assert r["iters"] == 28
+    ref = fot.fot_iterate(g, G, eps, 28)
+    assert abs(r["tv"] - sum(_dense_violation(ref["f"], ref["psi"], ref["a"], ref["b"], eps))) < 1e-12
+    # already below tol at the first check
+    assert fot.fot_iterate_tol(g, G, eps, max_iters, 10.0, k)["iters"] == k
+
+
 # P12: the dense autograd gradient of the phase loss (an independent dense implementation)
 # against central finite differences, and its phase against the separable oracle
 def test_p12_adjoint_oracle_vs_finite_differences():
