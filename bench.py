@@ -43,9 +43,14 @@ def _args():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping"],
                    help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
-                        "against looping single solves of the same problems")
+                        "against looping single solves of the same problems; stopping: the "
+                        "single workload solved to a marginal-violation tolerance")
+    p.add_argument("--tol", type=float, default=0.2,
+                   help="stopping workload: tolerance on sum |Gamma 1 - a|")
+    p.add_argument("--check-every", type=int, default=10,
+                   help="stopping workload: iterations between violation checks")
     return p.parse_args()
 
 
@@ -479,12 +484,76 @@ def run_batched(a):
     return 0
 
 
+def run_stopping(a):
+    """The single workload with the convergence stop: fot_solve_tol (at most --iters
+    iterations, a violation check every --check-every) + fot_phase per step, against
+    fot_solve with the same number of iterations (the cost of the checks)."""
+    import torch
+    from paper_2512_19072_gb300 import binding as B
+    w = _workload(a.n, a.iters)
+    n = a.n
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    prec = {"fp32": B.FOT_FP32, "fp32_dense": B.FOT_FP32_DENSE, "mixed": B.FOT_MIXED}[a.precision]
+    ctx = B.fot_create(n, n, prec)
+    phi, Dx, Dy = ctx.empty(), ctx.empty(), ctx.empty()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    done = [0, 0.0]
+
+    def step_tol():
+        done[0], done[1] = B.fot_solve_tol(ctx, g, G, w.eps, a.iters, a.tol, a.check_every)
+        B._check(B._lib.fot_phase(ctx._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
+
+    def step_fixed():
+        B.fot_solve(ctx, g, G, w.eps[:done[0]], done[0])   # one eps per iteration
+        B._check(B._lib.fot_phase(ctx._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
+
+    def timed(step):
+        for _ in range(a.warmup):
+            flush.zero_()
+            step()
+        ms = []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    clocks = _Clocks(torch.cuda.current_device())
+    ms_tol = timed(step_tol)
+    clk = clocks.stop()
+    iters, tv = done
+    ms_fixed = timed(step_fixed)
+    cfg = _config(w, n, a, 1)
+    cfg.update({"step": "fot_solve_tol (prep + at most %d iterations, a check every %d) + fot_phase"
+                        % (a.iters, a.check_every), "tol": a.tol, "check_every": a.check_every,
+                "iters_done": iters})
+    line = {"metric": "FOT Mpixel*iter/s to a marginal-violation tolerance", "value": n * n * iters / (ms_tol * 1e-3) / 1e6,
+            "unit": "Mpixel*iter/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_tol, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32" if a.precision == "mixed" else "f32", "data": "synthetic",
+            "config": cfg, "violation": tv, "fixed_iters_ms_per_step": ms_fixed,
+            "check_overhead": ms_tol / ms_fixed - 1.0, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":
         return run_batched(a)
+    if a.workload == "stopping":
+        return run_stopping(a)
     return run_gpu(a)
 
 

@@ -101,6 +101,25 @@ fot_status fot_solve(fot_ctx* ctx, const float* g, const float* G, double dx,
  * context holds (checkpoint / resume).  Same eps rules as fot_solve. */
 fot_status fot_resume(fot_ctx* ctx, const double* eps, int n_eps, int eps_units, int iters);
 
+/* Algorithm 1 with a convergence stop.  Sec. 2 names the total variation of the
+ * marginal-constraint violation as a convergence criterion; this call loads the problem and
+ * starts as fot_solve, then runs at most max_iters iterations in blocks of check_every, and
+ * after each block (and after the last allowed iteration) measures
+ *     tv = sum_jk | (Gamma 1)_jk - a_jk |,   Gamma = exp((f + psi - C) / eps_t),
+ * for the current iterate (f_t, psi_t); it stops at the first check with tv <= tol.  Right
+ * after a V-half the column sums of Gamma equal b (up to rounding), so this source half is
+ * the whole violation there.  The row sums are exp(f/eps + S(psi)) with S from one more
+ * u-half on the context's own passes (its precision), reduced in FP64: a check costs one
+ * half-step, two small reductions and one device-to-host read (synchronising).
+ *   eps: n_eps == 1 (fixed) or n_eps == max_iters (iteration t uses eps[t]); eps_units and dx
+ *   as in fot_solve.  max_iters >= 1, check_every >= 1, tol finite and >= 0, iters_out not
+ *   NULL: else FOT_EINVAL.  *iters_out receives the iterations done, *tv_out (may be NULL) the
+ *   last measured violation.  Afterwards the context holds the state fot_solve reaches after
+ *   *iters_out iterations (fot_loop_time then covers the last block). */
+fot_status fot_solve_tol(fot_ctx* ctx, const float* g, const float* G, double dx,
+                         const double* eps, int n_eps, int eps_units, int max_iters, double tol,
+                         int check_every, int* iters_out, double* tv_out);
+
 /* Wait for the context's stream; return the latched device status. */
 fot_status fot_sync(fot_ctx* ctx);
 

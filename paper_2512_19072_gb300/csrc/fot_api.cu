@@ -18,6 +18,7 @@ void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, doub
                   float* Dx, float* Dy);
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
 void fill(fot_ctx* c, float* p, size_t N, float v);
+void source_stats(fot_ctx* c, const float* f, const float* S, double eps, double* out);
 void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
                     const float* T, double eps, double* out);
 void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, float* phi);
@@ -320,13 +321,9 @@ static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int u
   return check_launch(c);
 }
 
-fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,
-                     int n_eps, int eps_units, int iters) {
-  if (!c || bad_ptr(g) || bad_ptr(G)) return FOT_EINVAL;
-  fot_status s = check_eps(eps, n_eps, iters);
-  if (s != FOT_OK) return s;
-  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
-  if (!isfinite(dx)) return FOT_EINVAL;
+// load the problem and the Algorithm 1 start (arguments already checked)
+static fot_status start_solve(fot_ctx* c, const float* g, const float* G, double dx,
+                              const double* eps, int eps_units) {
   FOT_CUDA(cudaSetDevice(c->device));
   FOT_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
   const double n = (double)(c->rows > c->cols ? c->rows : c->cols);
@@ -338,7 +335,54 @@ fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, cons
   c->have_problem = true;
   c->have_solution = false;
   c->sched.clear();
+  return FOT_OK;
+}
+
+fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,
+                     int n_eps, int eps_units, int iters) {
+  if (!c || bad_ptr(g) || bad_ptr(G)) return FOT_EINVAL;
+  fot_status s = check_eps(eps, n_eps, iters);
+  if (s != FOT_OK) return s;
+  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
+  if (!isfinite(dx)) return FOT_EINVAL;
+  s = start_solve(c, g, G, dx, eps, eps_units);
+  if (s != FOT_OK) return s;
   return run_iterations(c, eps, n_eps, eps_units, iters);
+}
+
+fot_status fot_solve_tol(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,
+                         int n_eps, int eps_units, int max_iters, double tol, int check_every,
+                         int* iters_out, double* tv_out) {
+  if (!c || bad_ptr(g) || bad_ptr(G) || !iters_out) return FOT_EINVAL;
+  if (max_iters < 1 || check_every < 1 || !(tol >= 0.0) || !isfinite(tol)) return FOT_EINVAL;
+  fot_status s = check_eps(eps, n_eps, max_iters);
+  if (s != FOT_OK) return s;
+  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
+  if (!isfinite(dx)) return FOT_EINVAL;
+  s = start_solve(c, g, G, dx, eps, eps_units);
+  if (s != FOT_OK) return s;
+  int done = 0;
+  double tv = INFINITY;
+  while (done < max_iters) {
+    const int k = max_iters - done < check_every ? max_iters - done : check_every;
+    s = run_iterations(c, n_eps == 1 ? eps : eps + done, n_eps == 1 ? 1 : k, eps_units, k);
+    if (s != FOT_OK) return s;
+    done += k;
+    // the row sums of Gamma(f, psi) at eps_last: S(psi) from one more u-half (its potentials
+    // are thrown away), then sum |exp(f/eps + S) - a| in FP64
+    half_step(c, c->psi, c->la, c->eps_last, c->tmp2, c->tmp);
+    double* out = c->red + 4 * c->red_blocks;
+    source_stats(c, c->f, c->tmp, c->eps_last, out);
+    double h[3];
+    FOT_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    s = read_latched(c);
+    if (s != FOT_OK) return s;
+    tv = h[0];
+    if (tv <= tol) break;
+  }
+  *iters_out = done;
+  if (tv_out) *tv_out = tv;
+  return FOT_OK;
 }
 
 fot_status fot_resume(fot_ctx* c, const double* eps, int n_eps, int eps_units, int iters) {

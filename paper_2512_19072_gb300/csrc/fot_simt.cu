@@ -344,6 +344,14 @@ __global__ void sum_triples_kernel(const double* __restrict__ part, int nparts, 
     for (int q = 0; q < 3; ++q) out[q] = s[q][0];
 }
 
+// out[0..2] = source {L1, mass, <f,a>} alone (the convergence check of fot_solve_tol)
+void source_stats(fot_ctx* c, const float* f, const float* S, double eps, double* out) {
+  const size_t N = (size_t)c->rows * c->cols;
+  marginal_partials_kernel<<<c->red_blocks, 256, 0, c->stream>>>(f, S, c->la, N, 1.0 / eps, c->red);
+  sum_triples_kernel<<<1, 256, 0, c->stream>>>(c->red, c->red_blocks, out);
+  c->launches += 2;
+}
+
 // out[0..2] = source {L1, mass, <f,a>}; out[3..5] = target {L1, mass, <psi,b>}
 void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
                     const float* T, double eps, double* out) {
