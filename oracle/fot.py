@@ -351,6 +351,31 @@ def dual_objective(f, psi, a, b, eps):
 
 
 # ----------------------------------------------------------------------------------------
+# L1 intensity loss of a phase solution (Sec. 5)
+# ----------------------------------------------------------------------------------------
+def intensity_loss(g, phi, G):
+    """|| I - b ||_1 with I = |F[g e^{2 pi i phi}]|^2 and b = G^2, both normalised to unit total
+    power (Sec. 5, the loss of the eps sweep), phi in cycles.  F is the 2-D DFT between the
+    centred grids of Sec. 2: x_j = (j - floor(n/2)) dx on the input plane and
+    X_L = (L - floor(n/2)) dX on the target plane with dx dX = 1/n, i.e.
+        F[h]_LM = sum_jk h_jk exp(-2 pi i ((j - c_r)(L - c_r)/n_r + (k - c_c)(M - c_c)/n_c)).
+    Written with the two DFT matrices (tiny and mid-size grids).  Returns (loss, I)."""
+    g = np.asarray(g, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    n_r, n_c = g.shape
+    jr = np.arange(n_r, dtype=np.float64) - n_r // 2
+    jc = np.arange(n_c, dtype=np.float64) - n_c // 2
+    Fr = np.exp(-2j * np.pi * np.outer(jr, jr) / n_r)     # [L, j]
+    Fc = np.exp(-2j * np.pi * np.outer(jc, jc) / n_c)     # [M, k]
+    field = g * np.exp(2j * np.pi * phi)
+    X = Fr @ field @ Fc.T
+    inten = np.abs(X) ** 2
+    inten = inten / inten.sum()
+    b = marginal(G)
+    return float(np.abs(inten - b).sum()), inten
+
+
+# ----------------------------------------------------------------------------------------
 # c-transform (eps -> 0 limit of a half-step)
 # ----------------------------------------------------------------------------------------
 def c_transform(pot):

@@ -304,6 +304,37 @@ def test_p13_stop_rule_against_dense_plan():
     assert fot.fot_iterate_tol(g, G, eps, max_iters, 10.0, k)["iters"] == k
 
 
+# P14: the L1 intensity loss (Sec. 5).  The centred DFT against numpy's FFT with the centring
+# done by index shifts, Parseval, and plane waves whose far field is one pixel.
+def test_p14_intensity_loss():
+    rng = np.random.default_rng(23)
+    for n_r, n_c in ((8, 8), (6, 9), (16, 12)):
+        g = rng.uniform(0.0, 1.0, size=(n_r, n_c))
+        phi = rng.normal(0.0, 2.0, size=(n_r, n_c))
+        G = rng.uniform(0.0, 1.0, size=(n_r, n_c))
+        loss, inten = fot.intensity_loss(g, phi, G)
+        field = g * np.exp(2j * np.pi * phi)
+        X = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(field)))
+        ref = np.abs(X) ** 2
+        assert np.abs(inten - ref / ref.sum()).max() < 1e-13
+        assert abs(ref.sum() - n_r * n_c * (g ** 2).sum()) < 1e-9 * ref.sum()      # Parseval
+        b = G ** 2 / (G ** 2).sum()
+        assert abs(loss - np.abs(ref / ref.sum() - b).sum()) < 1e-13
+    # a uniform beam with the linear phase x . X0 lands on the single target pixel X0
+    n = 16
+    j = np.arange(n) - n // 2
+    for L0, M0 in ((3, -5), (0, 0), (-8, 7)):
+        phi = (np.add.outer(j * L0, j * M0)) / n          # cycles: (x X0) with dx dX = 1/n
+        G = np.zeros((n, n))
+        G[L0 + n // 2, M0 + n // 2] = 1.0
+        loss, inten = fot.intensity_loss(np.ones((n, n)), phi, G)
+        assert loss < 1e-12 and abs(inten[L0 + n // 2, M0 + n // 2] - 1.0) < 1e-12
+    # and misses a target one pixel away entirely: the loss is the maximum, 2
+    G = np.zeros((n, n))
+    G[n // 2 + 1, n // 2] = 1.0
+    assert abs(fot.intensity_loss(np.ones((n, n)), np.zeros((n, n)), G)[0] - 2.0) < 1e-12
+
+
 # P12: the dense autograd gradient of the phase loss (an independent dense implementation)
 # against central finite differences, and its phase against the separable oracle
 def test_p12_adjoint_oracle_vs_finite_differences():
