@@ -43,10 +43,11 @@ def _args():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity"],
                    help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
                         "against looping single solves of the same problems; stopping: the "
-                        "single workload solved to a marginal-violation tolerance")
+                        "single workload solved to a marginal-violation tolerance; intensity: the "
+                        "L1 intensity loss of that workload's phase")
     p.add_argument("--tol", type=float, default=0.2,
                    help="stopping workload: tolerance on sum |Gamma 1 - a|")
     p.add_argument("--check-every", type=int, default=10,
@@ -546,6 +547,54 @@ def run_stopping(a):
     return 0
 
 
+def run_intensity(a):
+    """The L1 intensity loss (Sec. 5) of the single workload's phase after one solve: each
+    step is one fot_intensity_loss call (two FFT passes and two reductions), timed with CUDA
+    events, L2 flushed between steps.  Algorithmic traffic 44 n^2 bytes per call: the row
+    pass reads log a and phi and writes the spectrum (8 + 8), the column pass reads it and
+    writes I (8 + 4), the reductions read I, read log b and I and rewrite I (4 + 12)."""
+    import torch
+    from paper_2512_19072_gb300 import binding as B
+    w = _workload(a.n, a.iters)
+    n = a.n
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    ctx = B.fot_create(n, n, B.FOT_MIXED)
+    B.fot_solve(ctx, g, G, w.eps, a.iters)
+    phi, _, _ = B.fot_phase(ctx)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        loss = B.fot_intensity_loss(ctx, phi)
+    ms = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loss = B.fot_intensity_loss(ctx, phi)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    nbytes = 44.0 * n * n
+    peaks, peak_src = _peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    line = {"metric": "FOT L1 intensity loss evaluations/s", "value": 1e3 / t, "unit": "evaluations/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": w.name, "n": n, "phase_from": f"fot_solve ({a.iters} iterations, mixed) + fot_phase",
+                                            "l2": "flushed between steps (256 MB write)"},
+            "loss": loss,
+            "roofline": {"bound": "hbm", "achieved": nbytes / (t * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": nbytes / (t * 1e-3) / 1e9 / peak, "traffic": None,
+                         "work": "44 n^2 bytes per evaluation", "peak_source": "STREAM copy, " + peak_src}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -554,6 +603,8 @@ def main():
         return run_batched(a)
     if a.workload == "stopping":
         return run_stopping(a)
+    if a.workload == "intensity":
+        return run_intensity(a)
     return run_gpu(a)
 
 

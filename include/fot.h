@@ -154,6 +154,19 @@ fot_status fot_moments(fot_ctx* ctx, const float* psi, const float* logsum_u, do
  * <f,a> + <psi,b> - eps sum Gamma + eps when dual_out != NULL.  Synchronising. */
 fot_status fot_marginal_error(fot_ctx* ctx, double* l1_out, double* dual_out);
 
+/* L1 intensity loss of a phase solution (Sec. 5, the loss of the eps sweep):
+ *   loss = sum_LM | I_LM - b_LM |,   I = |F[g e^{2 pi i phi}]|^2 / sum_LM |F[g e^{2 pi i phi}]|^2,
+ * for the loaded problem's input beam g (taken as sqrt(a), a = g^2 / sum g^2: the scale
+ * cancels), the phase phi (device, rows x cols, in cycles, e.g. from fot_phase), the target
+ * b = G^2 / sum G^2, and F the 2-D DFT between the centred grids of Sec. 2:
+ *   F[h]_LM = sum_jk h_jk exp(-2 pi i ((j - r/2)(L - r/2)/rows + (k - c/2)(M - c/2)/cols)),
+ * r = rows, c = cols (x_j = (j - rows/2) dx, X_L = (L - rows/2) dX with dx dX = 1/rows).
+ * rows and cols must be powers of two in [2, 4096] (else FOT_EUNSUPPORTED); phi and loss_out
+ * not NULL (else FOT_EINVAL); a problem loaded by fot_solve / fot_set_problem (else
+ * FOT_ESTATE).  intensity_out (device, rows x cols, may be NULL) receives I.  Uses the
+ * context's scratch buffers, not its potentials; FP32 transforms, FP64 sums.  Synchronising. */
+fot_status fot_intensity_loss(fot_ctx* ctx, const float* phi, double* loss_out, float* intensity_out);
+
 /* One half-step from caller potentials, for verification and custom loops:
  *   fot_u_update: f = eps (log a - S), S = log(Lambda exp(psi/eps) Lambda)   (Eq. 7)
  *   fot_v_update: psi = eps (log b - T), T = log(Lambda exp(f/eps) Lambda)   (Eq. 8)

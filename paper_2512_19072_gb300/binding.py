@@ -49,6 +49,7 @@ _SIGS = {
     "fot_set_potentials": (_I, [_P, _P, _P]),
     "fot_phase": (_I, [_P, _P, _P, _P]),
     "fot_marginal_error": (_I, [_P, _DP, _DP]),
+    "fot_intensity_loss": (_I, [_P, _P, _DP, _P]),
     "fot_moments": (_I, [_P, _P, _P, _D, _D, _P, _P, _P]),
     "fot_u_update": (_I, [_P, _P, _D, _P, _P]),
     "fot_v_update": (_I, [_P, _P, _D, _P, _P]),
@@ -210,6 +211,17 @@ def fot_marginal_error(ctx):
     _check(_lib.fot_marginal_error(ctx._h, ctypes.byref(l1), ctypes.byref(dual)),
            "fot_marginal_error")
     return l1.value, dual.value
+
+
+def fot_intensity_loss(ctx, phi, with_intensity=False):
+    """L1 intensity loss of the phase phi (cycles) for the loaded problem; with_intensity also
+    returns the normalised far-field intensity."""
+    out = ctypes.c_double()
+    inten = ctx.empty() if with_intensity else None
+    ctx._sync_stream()
+    _check(_lib.fot_intensity_loss(ctx._h, _ptr(phi), ctypes.byref(out), _ptr(inten)),
+           "fot_intensity_loss")
+    return (out.value, inten) if with_intensity else out.value
 
 
 def fot_u_update(ctx, psi, eps, with_logsum=False):

@@ -19,6 +19,8 @@ void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, doub
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
 void fill(fot_ctx* c, float* p, size_t N, float v);
 void source_stats(fot_ctx* c, const float* f, const float* S, double eps, double* out);
+bool intensity_supported(int rows, int cols);
+void intensity_loss_gpu(fot_ctx* c, const float* phi, double* out);
 void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
                     const float* T, double eps, double* out);
 void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, float* phi);
@@ -467,6 +469,24 @@ fot_status fot_marginal_error(fot_ctx* c, double* l1_out, double* dual_out) {
   if (s != FOT_OK) return s;
   *l1_out = h[0] + h[3];
   if (dual_out) *dual_out = h[2] + h[5] - e * h[1] + e;
+  return FOT_OK;
+}
+
+fot_status fot_intensity_loss(fot_ctx* c, const float* phi, double* loss_out, float* intensity_out) {
+  if (!c || bad_ptr(phi) || !loss_out) return FOT_EINVAL;
+  if (!c->have_problem) return FOT_ESTATE;
+  if (!intensity_supported(c->rows, c->cols)) return FOT_EUNSUPPORTED;
+  FOT_CUDA(cudaSetDevice(c->device));
+  double* out = c->red + 4 * c->red_blocks + 8;      // [0] loss, [1] total power
+  intensity_loss_gpu(c, phi, out);
+  if (intensity_out)
+    FOT_CUDA(cudaMemcpyAsync(intensity_out, c->tmp, (size_t)c->rows * c->cols * sizeof(float),
+                             cudaMemcpyDeviceToDevice, c->stream));
+  double h[2];
+  FOT_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  fot_status s = read_latched(c);
+  if (s != FOT_OK) return s;
+  *loss_out = h[0];
   return FOT_OK;
 }
 
