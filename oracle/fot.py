@@ -182,6 +182,34 @@ def fot_iterate_expdomain(g, G, eps, iters):
     return u, V, Lam_r, Lam_c
 
 
+def cfot_iterate(g, G, eps, iters):
+    """cFOT (Sec. 3.1): Algorithm 1 in the exponential domain with every product by the Toeplitz
+    matrix Lambda replaced by a linear convolution with lambda_j = exp(-j^2 / (2 eps)),
+    j = -(n-1) .. n-1 (eps in px^2):
+        u = a / (lambda * V * lambda),   V = b / (lambda * u * lambda),
+    the convolutions along the columns and along the rows, V0 = 1/(n_r n_c).  Each convolution
+    is np.convolve over one line, keeping the n outputs aligned with the input grid.
+    Returns u, V and S_last = log(lambda * V_prev * lambda) of the last u-update."""
+    a, b = marginal(g), marginal(G)
+    n_r, n_c = a.shape
+    lam_r = np.exp(-np.arange(-(n_r - 1), n_r, dtype=np.float64) ** 2 / (2.0 * eps))
+    lam_c = np.exp(-np.arange(-(n_c - 1), n_c, dtype=np.float64) ** 2 / (2.0 * eps))
+
+    def kernel_apply(X):
+        # rows: (X * lambda)[j, k] = sum_M X[j, M] lambda_{k - M}; then the columns likewise
+        Y = np.stack([np.convolve(X[j], lam_c)[n_c - 1:2 * n_c - 1] for j in range(n_r)])
+        return np.stack([np.convolve(Y[:, k], lam_r)[n_r - 1:2 * n_r - 1] for k in range(n_c)], 1)
+
+    V = np.full((n_r, n_c), 1.0 / (n_r * n_c))
+    u = S = None
+    for _ in range(iters):
+        KV = kernel_apply(V)
+        u = a / KV
+        S = np.log(KV)
+        V = b / kernel_apply(u)
+    return u, V, S
+
+
 # ----------------------------------------------------------------------------------------
 # phase recovery: Eqs. 9-10 and the trapezoid integration step of Algorithm 1
 # ----------------------------------------------------------------------------------------

@@ -335,6 +335,22 @@ def test_p14_intensity_loss():
     assert abs(fot.intensity_loss(np.ones((n, n)), np.zeros((n, n)), G)[0] - 2.0) < 1e-12
 
 
+# P15: cFOT (Sec. 3.1).  The linear convolutions against the Toeplitz products of the literal
+# exponential-domain Algorithm 1, and against the log-domain iterate (same iteration, so same
+# potentials, f = eps log u, psi = eps log V, and the same S_last).
+def test_p15_cfot_equals_toeplitz_products():
+    rng = np.random.default_rng(29)
+    for (n_r, n_c), eps, iters in (((6, 9), 4.0, 5), ((12, 10), 20.0, 8)):
+        g, G = _rand_masses(rng, n_r, n_c)
+        u, V, S = fot.cfot_iterate(g, G, eps, iters)
+        u2, V2, _, _ = fot.fot_iterate_expdomain(g, G, eps, iters)
+        assert np.abs(u / u2 - 1).max() < 1e-12 and np.abs(V / V2 - 1).max() < 1e-12
+        r = fot.fot_iterate(g, G, eps, iters)
+        assert np.abs(eps * np.log(u) - r["f"]).max() < 1e-9 * np.abs(r["f"]).max()
+        assert np.abs(eps * np.log(V) - r["psi"]).max() < 1e-9 * np.abs(r["psi"]).max()
+        assert np.abs(S - r["S_last"]).max() < 1e-10
+
+
 # P12: the dense autograd gradient of the phase loss (an independent dense implementation)
 # against central finite differences, and its phase against the separable oracle
 def test_p12_adjoint_oracle_vs_finite_differences():
