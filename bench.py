@@ -43,11 +43,13 @@ def _args():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity", "cfot"],
                    help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
                         "against looping single solves of the same problems; stopping: the "
                         "single workload solved to a marginal-violation tolerance; intensity: the "
-                        "L1 intensity loss of that workload's phase")
+                        "L1 intensity loss of that workload's phase; cfot: cFOT against FOT per "
+                        "iteration on beams over a flat floor")
+    p.add_argument("--cfot-eps", type=float, default=1e5, help="cfot workload: eps in px^2")
     p.add_argument("--tol", type=float, default=0.2,
                    help="stopping workload: tolerance on sum |Gamma 1 - a|")
     p.add_argument("--check-every", type=int, default=10,
@@ -595,6 +597,68 @@ def run_intensity(a):
     return 0
 
 
+def run_cfot(a):
+    """cFOT (FFT convolutions, exponential domain, FP32) against FOT (banded passes, the
+    context's mixed form) per iteration, on two beams over a flat floor at n^2 and a large
+    eps (cFOT fails at the benchmark workload's eps: its u, V leave the FP32 range).  Each step
+    is one solve of --iters iterations, L2 flushed between steps."""
+    import torch
+    from paper_2512_19072_gb300 import binding as B
+    n = a.n
+    j = np.arange(n)[:, None]
+    k = np.arange(n)[None, :]
+    g = torch.from_numpy((np.exp(-((j - 0.45 * n) ** 2 + (k - 0.55 * n) ** 2) / (2 * (n / 5) ** 2)) + 1.0)
+                         .astype(np.float32)).cuda()
+    G = torch.from_numpy((np.exp(-((j - 0.55 * n) ** 2 + (k - 0.40 * n) ** 2) / (2 * (n / 4) ** 2)) + 1.0)
+                         .astype(np.float32)).cuda()
+    ctx = B.fot_create(n, n, B.FOT_MIXED)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(a.warmup):
+            fn()
+        B.fot_sync(ctx)
+        ms = []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        B.fot_sync(ctx)
+        return statistics.median(ms)
+
+    failed = None
+    try:
+        t_c = timed(lambda: B.fot_cfot_solve(ctx, g, G, a.cfot_eps, a.iters))
+        l1_c, _ = B.fot_marginal_error(ctx)
+        _, psi_c = B.fot_potentials(ctx)
+    except B.FotError as e:                  # the exponential-domain iteration left FP32
+        failed, t_c, l1_c, psi_c = str(e), float("nan"), None, None
+    t_f = timed(lambda: B.fot_solve(ctx, g, G, a.cfot_eps, a.iters))
+    l1_f, _ = B.fot_marginal_error(ctx)
+    _, psi_f = B.fot_potentials(ctx)
+    diff = None
+    if psi_c is not None:
+        fin = torch.isfinite(psi_f)
+        diff = float((psi_c[fin] - psi_f[fin]).abs().max() / psi_f[fin].abs().max())
+    line = {"metric": "cFOT Mpixel*iter/s (FFT convolutions) vs FOT", "value": n * n * a.iters / (t_c * 1e-3) / 1e6,
+            "unit": "Mpixel*iter/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_c,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "two beams over a flat floor", "n": n, "iters_per_solve": a.iters,
+                       "eps_px2": a.cfot_eps, "l2": "flushed between steps (256 MB write)"},
+            "cfot_ms_per_iter": t_c / a.iters, "fot_mixed_ms_per_iter": t_f / a.iters,
+            "marginal_l1": {"cfot": l1_c, "fot": l1_f}, "psi_rel_diff": diff, "cfot_failed": failed}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -605,6 +669,8 @@ def main():
         return run_stopping(a)
     if a.workload == "intensity":
         return run_intensity(a)
+    if a.workload == "cfot":
+        return run_cfot(a)
     return run_gpu(a)
 
 

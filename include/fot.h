@@ -120,6 +120,22 @@ fot_status fot_solve_tol(fot_ctx* ctx, const float* g, const float* G, double dx
                          const double* eps, int n_eps, int eps_units, int max_iters, double tol,
                          int check_every, int* iters_out, double* tv_out);
 
+/* cFOT (Sec. 3.1): the same problem, start and eps rules as fot_solve, but the iterations run
+ * Algorithm 1 in the exponential domain with every Lambda product replaced by a linear
+ * convolution with lambda_j = exp(-j^2 / (2 eps)), j = -(n-1) .. n-1, along the columns and
+ * the rows, evaluated with FFTs (O(n^2 log n) per iteration instead of O(n^3)):
+ *     u = a / (lambda * V * lambda),   V = b / (lambda * u * lambda),   V0 = 1/(rows*cols).
+ * FP32 throughout.  Afterwards the context holds f = eps log u, psi = eps log V (px^2, -inf on
+ * zero mass) and S_last = log(lambda * V_prev * lambda) of the last u-update, so fot_potentials,
+ * fot_phase, fot_marginal_error and fot_intensity_loss apply; fot_backward does not
+ * (FOT_ESTATE).  Like any exponential-domain iteration it fails once eps is small against the
+ * spread of the potentials (u, V outside the FP32 range, or FFT rounding, a few ulp of a line's
+ * largest value, swamping its small entries): a non-positive or non-finite convolution where
+ * the marginal has mass latches FOT_ENONFINITE.  rows, cols in [2, 2048] (FFT length up to 4096;
+ * else FOT_EUNSUPPORTED); iters >= 1.  Allocates a 32 KB spectrum buffer on its first call. */
+fot_status fot_cfot_solve(fot_ctx* ctx, const float* g, const float* G, double dx,
+                          const double* eps, int n_eps, int eps_units, int iters);
+
 /* Wait for the context's stream; return the latched device status. */
 fot_status fot_sync(fot_ctx* ctx);
 

@@ -43,6 +43,7 @@ _SIGS = {
     "fot_set_problem": (_I, [_P, _P, _P]),
     "fot_solve": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I]),
     "fot_resume": (_I, [_P, _DP, _I, _I, _I]),
+    "fot_cfot_solve": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I]),
     "fot_solve_tol": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
     "fot_sync": (_I, [_P]),
     "fot_potentials": (_I, [_P, _P, _P]),
@@ -152,6 +153,15 @@ def fot_solve(ctx, g, G, eps, iters=None, dx=0.0, eps_units=FOT_EPS_PX2):
     ctx._sync_stream()
     _check(_lib.fot_solve(ctx._h, _ptr(g), _ptr(G), float(dx), ep, ne, eps_units, int(iters)),
            "fot_solve")
+
+
+def fot_cfot_solve(ctx, g, G, eps, iters=None, dx=0.0, eps_units=FOT_EPS_PX2):
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    ctx._sync_stream()
+    _check(_lib.fot_cfot_solve(ctx._h, _ptr(g), _ptr(G), float(dx), ep, ne, eps_units, int(iters)),
+           "fot_cfot_solve")
 
 
 def fot_solve_tol(ctx, g, G, eps, max_iters, tol, check_every, dx=0.0, eps_units=FOT_EPS_PX2):

@@ -20,6 +20,9 @@ void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, f
 void fill(fot_ctx* c, float* p, size_t N, float v);
 void source_stats(fot_ctx* c, const float* f, const float* S, double eps, double* out);
 bool intensity_supported(int rows, int cols);
+bool cfot_supported(int rows, int cols);
+void cfot_run(fot_ctx* c, const double* eps_px, int iters);
+size_t cfot_spectrum_floats();
 void intensity_loss_gpu(fot_ctx* c, const float* phi, double* out);
 void marginal_stats(fot_ctx* c, const float* f, const float* S, const float* psi,
                     const float* T, double eps, double* out);
@@ -190,6 +193,7 @@ void fot_destroy(fot_ctx* c) {
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (c->red) cudaFree(c->red);
+  if (c->lam_hat) cudaFree(c->lam_hat);
   if (c->err) cudaFree(c->err);
   if (c->terms) cudaFree(c->terms);
   if (c->ev_loop0) cudaEventDestroy(c->ev_loop0);
@@ -350,6 +354,34 @@ fot_status fot_solve(fot_ctx* c, const float* g, const float* G, double dx, cons
   s = start_solve(c, g, G, dx, eps, eps_units);
   if (s != FOT_OK) return s;
   return run_iterations(c, eps, n_eps, eps_units, iters);
+}
+
+fot_status fot_cfot_solve(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,
+                          int n_eps, int eps_units, int iters) {
+  if (!c || bad_ptr(g) || bad_ptr(G) || iters < 1) return FOT_EINVAL;
+  fot_status s = check_eps(eps, n_eps, iters);
+  if (s != FOT_OK) return s;
+  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
+  if (!isfinite(dx)) return FOT_EINVAL;
+  if (!cfot_supported(c->rows, c->cols)) return FOT_EUNSUPPORTED;
+  FOT_CUDA(cudaSetDevice(c->device));
+  if (!c->lam_hat && cudaMalloc((void**)&c->lam_hat, cfot_spectrum_floats() * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    c->lam_hat = nullptr;
+    return FOT_ENOMEM;
+  }
+  s = start_solve(c, g, G, dx, eps, eps_units);
+  if (s != FOT_OK) return s;
+  std::vector<double> e((size_t)iters);
+  for (int t = 0; t < iters; ++t) e[(size_t)t] = eps_px(c, eps[n_eps == 1 ? 0 : t], eps_units);
+  const int64_t l0 = c->launches;
+  cudaEventRecord(c->ev_loop0, c->stream);
+  cfot_run(c, e.data(), iters);
+  cudaEventRecord(c->ev_loop1, c->stream);
+  c->loop_passes = c->launches - l0;
+  c->eps_last = e[(size_t)iters - 1];
+  c->have_solution = true;              // no schedule recorded: fot_backward does not apply
+  return check_launch(c);
 }
 
 fot_status fot_solve_tol(fot_ctx* c, const float* g, const float* G, double dx, const double* eps,

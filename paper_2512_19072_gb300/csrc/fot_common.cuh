@@ -79,6 +79,7 @@ struct fot_ctx {
   float* col_phi = nullptr;  // rows: phase along the centre column
   float* plan = nullptr;     // per-(row, 16-output tile) window plan of a banded pass, 3 words each
   double* red = nullptr;     // reduction scratch (partials + results)
+  float* lam_hat = nullptr;  // cFOT: the spectra of lambda (allocated by the first cFOT solve)
   int* err = nullptr;        // latched device status
   unsigned long long* terms = nullptr;  // device counters of evaluated (row, output, m) terms on
                                         // the CUDA cores: [0] banded GEMM, [1] exact windows
