@@ -491,8 +491,8 @@ int64_t tc_terms(fot_ctx* c) {
 // Tile width of a tensor-core pass for a problem with kernel constant c: the widest TN in
 // {64, 32} whose tile is expected to meet the tilt bound |kap| W c <= kTiltMaxTC with room to
 // spare: W is taken as twice the window of a smooth potential (the tile plus sqrt(kCut / c) on
-// each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to whole
-// stages, since the hull of a tile's windows grows where the transport map jumps across
+// each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to a multiple
+// of 64 positions, since the hull of a tile's windows grows where the transport map jumps across
 // zero-mass gaps; else 16 when a 16-wide tile can meet the bound at all (a taken tile has
 // W >= kRouteKC); else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
 int tc_width_for(float c) {
