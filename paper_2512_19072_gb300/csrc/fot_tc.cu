@@ -493,8 +493,8 @@ int64_t tc_terms(fot_ctx* c) {
 // spare: W is taken as twice the window of a smooth potential (the tile plus sqrt(kCut / c) on
 // each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to a multiple
 // of 64 positions, since the hull of a tile's windows grows where the transport map jumps across
-// zero-mass gaps; else 16 when a 16-wide tile can meet the bound at all (a taken tile has
-// W >= kRouteKC); else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
+// zero-mass gaps; else 16 when a 16-wide tile meets the bound with a window of kRouteKC
+// positions; else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
 int tc_width_for(float c) {
   for (int tn = 64; tn >= 32; tn /= 2) {
     const float w = (float)tn + 2.f * sqrtf(kCut / c);
