@@ -101,7 +101,7 @@ fot_status fot_solve(fot_ctx* ctx, const float* g, const float* G, double dx,
  * context holds (checkpoint / resume).  Same eps rules as fot_solve. */
 fot_status fot_resume(fot_ctx* ctx, const double* eps, int n_eps, int eps_units, int iters);
 
-/* Algorithm 1 with a convergence stop.  Sec. 2 names the total variation of the
+/* Algorithm 1 with a convergence stop.  Sec. 3 names the total variation of the
  * marginal-constraint violation as a convergence criterion; this call loads the problem and
  * starts as fot_solve, then runs at most max_iters iterations in blocks of check_every, and
  * after each block (and after the last allowed iteration) measures

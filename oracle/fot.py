@@ -333,14 +333,14 @@ def marginal_l1(f, psi, a, b, eps):
 
 def source_violation(f, psi, a, eps):
     """||Gamma 1 - a||_1: the source half of the total variation of the marginal violation
-    (the convergence measure Sec. 2 names).  Right after a V-half the target half is zero up to
+    (the convergence measure Sec. 3 names).  Right after a V-half the target half is zero up to
     rounding (psi makes the column sums equal b), so it is the whole measure there."""
     row, _ = plan_marginals(f, psi, eps)
     return float(np.abs(row - a).sum())
 
 
 def fot_iterate_tol(g, G, eps, max_iters, tol, check_every):
-    """Algorithm 1's loop with a convergence stop (Sec. 2): after every check_every iterations
+    """Algorithm 1's loop with a convergence stop (Sec. 3): after every check_every iterations
     (and after the last allowed one) measure the marginal violation of the current iterate
     (f_t, psi_t) at eps_t and stop at the first check where it is <= tol.
 

@@ -1,4 +1,4 @@
-"""Convergence stop (Sec. 2: total variation of the marginal violation) through the C ABI,
+"""Convergence stop (Sec. 3: total variation of the marginal violation) through the C ABI,
 against the oracle's fot_iterate_tol on the same seeded inputs.
 
 The tolerances sit between the oracle's violations at two consecutive checks, with a margin

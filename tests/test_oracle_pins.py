@@ -253,7 +253,7 @@ def test_marginal_l1_matches_dense_plan():
     assert abs(fot.dual_objective(r["f"], r["psi"], r["a"], r["b"], eps) - D) < 1e-12
 
 
-# P13: the convergence stop (Sec. 2).  The source violation against the row sums of the dense
+# P13: the convergence stop (Sec. 3).  The source violation against the row sums of the dense
 # plan Gamma = exp((f + psi - C)/eps) (the target half vanishing after a V-half), and the stop
 # against the violations of the dense plan at the checks before and at it.
 def _dense_violation(f, psi, a, b, eps):
