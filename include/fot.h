@@ -197,21 +197,25 @@ fot_status fot_v_update(fot_ctx* ctx, const float* f_in, double eps, float* psi_
  * callers that must not allocate device memory once they are running, for example a
  * real-time hologram loop that reserves all of its memory at start-up because cudaMalloc
  * can synchronise the device and stall the loop, or a plug-in whose host owns every
- * device allocation through its own allocator.  It computes the same update as
- * fot_u_update, f = eps (log_a - S) with S = log(Lambda exp(psi/eps) Lambda) (Eq. 7), but
- * needs no fot_ctx: the caller passes every input and output (device, rows x cols float32:
- * psi_in in px^2, log_a = natural log of the normalised source marginal a = g^2/sum g^2,
- * -INFINITY where a = 0; f_out; logsum_out may be NULL), and the intermediate lives in a
- * static device array of FOT_NOALLOC_MAX_PIXELS floats (4 MiB) that every GPU loading this
- * library holds until the process exits.  Nothing is allocated: no cudaMalloc, no cudaFree,
- * no allocating library call.
+ * device allocation through its own allocator.  It gives the same mathematical result as
+ * fot_u_update, f = eps (log_a - S) with S = log(Lambda exp(psi/eps) Lambda), but through
+ * a different kernel: the dense exact FP32 pass of FOT_FP32_DENSE (every output scans every
+ * term, one exponential each: O(rows * cols * (rows + cols)) work, much slower than the
+ * banded or tensor-core passes of fot_u_update at large sizes; results agree to FP32
+ * rounding).  It needs no fot_ctx: the caller passes every input and output (device,
+ * rows x cols float32: psi_in in px^2, log_a = natural log of the normalised source marginal
+ * a = g^2/sum g^2, -INFINITY where a = 0; f_out; logsum_out may be NULL), and the
+ * intermediate lives in a static device array of FOT_NOALLOC_MAX_PIXELS floats (4 MiB) that
+ * every GPU loading this library holds until the process exits.  Nothing is allocated: no
+ * cudaMalloc, no cudaFree, no allocating library call.
  *  - rows * cols > FOT_NOALLOC_MAX_PIXELS, or rows / cols outside [1, 4096]: FOT_EINVAL.
  *  - Runs on the current device, enqueued on cuda_stream (NULL = legacy default stream);
- *    asynchronous.  Non-finite results show up as non-finite values in f_out.
- *  - The first call on a device looks up the static array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call before any
- *    stream capture begins.  The host-side cache of that address is not thread-safe for a
- *    device's first call.
+ *    asynchronous.  Nothing is read back, so device-side problems are not reported as a
+ *    status: a non-finite result shows up as a non-finite value in f_out.
+ *  - The first call on a device does a one-time set-up with that device current: it looks
+ *    up the static array's device address (cudaGetSymbolAddress) and raises the pass
+ *    kernels' shared-memory limit; make that first call before any stream capture begins.
+ *    The host-side cache of that set-up is not thread-safe for a device's first call.
  *  - Every call shares the one array and it keeps the last call's contents: calls whose
  *    work overlaps on the GPU (different streams, or different host threads) race on it. */
 #define FOT_NOALLOC_MAX_PIXELS (1024 * 1024)
@@ -289,7 +293,8 @@ fot_status fot_work_split(fot_ctx* ctx, int64_t* out4);
 
 /* Kernel classes of fot_kernel_times. */
 enum {
-  FOT_KERNEL_PLAN = 0,     /* window plan of a banded pass */
+  FOT_KERNEL_PLAN = 0,     /* window plan of a banded pass (and the B-operand table of the
+                              tensor-core pass, written when eps changes) */
   FOT_KERNEL_BAND = 1,     /* banded pass on the CUDA cores (tilted-GEMM and exact-window items) */
   FOT_KERNEL_TENSOR = 2,   /* tensor-core banded pass */
   FOT_KERNEL_DENSE = 3,    /* dense exact pass */

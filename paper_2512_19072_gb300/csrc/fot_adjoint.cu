@@ -27,6 +27,7 @@
 #include "fot_common.cuh"
 
 namespace fot {
+void tc_begin(fot_ctx* c);
 void half_step_dispatch(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
                         float* logsum);
 void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, double dx, float* Dx, float* Dy);
@@ -242,6 +243,7 @@ extern "C" fot_status fot_backward(fot_ctx* c, const float* g, const float* G, c
     return FOT_ENOMEM;
   }
   const dim3 gN = grid_for(N);
+  if (c->tc) tc_begin(c);
   fill(c, neg_inf, N, -INFINITY);
   cudaMemsetAsync(psib, 0, B, s);
   cudaMemsetAsync(fb, 0, B, s);

@@ -14,6 +14,7 @@
 namespace fot {
 void half_step_simt(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                     float* pot_out, float* logsum, float* tmp);
+cudaError_t simt_configure();
 void moments_simt(fot_ctx* c, const float* psi, const float* S, double eps, double dx,
                   float* Dx, float* Dy);
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
@@ -37,6 +38,7 @@ void tc_destroy(fot_ctx* c);
 void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                   float* pot_out, float* logsum);
 int64_t tc_terms(fot_ctx* c);
+void tc_begin(fot_ctx* c);
 }  // namespace fot
 
 using namespace fot;
@@ -157,8 +159,10 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   bool ok = true;
   for (float** b : bufs) ok = ok && cudaMalloc((void**)b, N * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->col_phi, (size_t)rows * sizeof(float)) == cudaSuccess;
-  // the per-(row, 16-output tile) plan of the larger banded pass (3 words each)
-  const size_t plan_words = 3 * std::max((size_t)rows * ((cols + 15) / 16), (size_t)cols * ((rows + 15) / 16));
+  // the per-(16-output tile, row) plan of the larger banded pass (3 words each; rows padded to
+  // a multiple of 128, the plan's tile-major stride)
+  const size_t pr = (size_t)(rows + 127) / 128 * 128, pc = (size_t)(cols + 127) / 128 * 128;
+  const size_t plan_words = 3 * std::max(pr * ((cols + 15) / 16), pc * ((rows + 15) / 16));
   ok = ok && cudaMalloc((void**)&c->plan, plan_words * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->red, (size_t)(4 * c->red_blocks + 16) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc((void**)&c->err, sizeof(int)) == cudaSuccess;
@@ -166,6 +170,11 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   if (ok) ok = cudaMemsetAsync(c->terms, 0, 2 * sizeof(unsigned long long), c->stream) == cudaSuccess;
   if (ok) ok = cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) == cudaSuccess;
   if (ok) ok = cudaEventCreate(&c->ev_loop0) == cudaSuccess && cudaEventCreate(&c->ev_loop1) == cudaSuccess;
+  if (ok && simt_configure() != cudaSuccess) {   // per-device kernel attributes
+    cudaGetLastError();
+    fot_destroy(c);
+    return FOT_ECUDA;
+  }
   if (ok && precision == FOT_MIXED) {
     if (!tc_supported(rows, cols)) {
       fot_destroy(c);
@@ -188,6 +197,8 @@ void fot_destroy(fot_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->tc) tc_destroy(c);
   ktimer_free(c);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   float* bufs[] = {c->la, c->lb, c->f, c->psi, c->R, c->R2, c->S_last, c->tmp, c->tmp2, c->phi,
                    c->col_phi, c->plan};
   for (float* b : bufs)
@@ -307,21 +318,76 @@ static void half_step(fot_ctx* c, const float* pot_in, const float* lmarg, doubl
     half_step_band(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
 }
 
-static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int units, int iters) {
-  const int64_t l0 = c->launches;
-  g_ktimer = c->ktimer;                    // null unless kernel timing is on
-  cudaEventRecord(c->ev_loop0, c->stream);
+// the loop of Algorithm 1 for per-iteration eps e (px^2), enqueued on c->stream
+static void loop_body(fot_ctx* c, const std::vector<double>& e) {
+  const int iters = (int)e.size();
+  if (c->tc) tc_begin(c);
   for (int t = 0; t < iters; ++t) {
-    const double e = eps_px(c, eps[n_eps == 1 ? 0 : t], units);
     // Eq. 7: f = eps (log a - log(Lambda V Lambda)); keep S of the last u-update (Eqs. 9-10)
-    half_step(c, c->psi, c->la, e, c->f, t == iters - 1 ? c->S_last : nullptr);
+    half_step(c, c->psi, c->la, e[(size_t)t], c->f, t == iters - 1 ? c->S_last : nullptr);
     // Eq. 8: psi = eps (log b - log(Lambda u Lambda))
-    half_step(c, c->f, c->lb, e, c->psi, nullptr);
-    c->eps_last = e;
-    c->sched.push_back(e);
+    half_step(c, c->f, c->lb, e[(size_t)t], c->psi, nullptr);
   }
-  cudaEventRecord(c->ev_loop1, c->stream);
-  g_ktimer = nullptr;
+}
+
+// Capture the loop for schedule e into c->loop_exec (on the context's private stream: the
+// legacy default stream cannot be captured).  False when capture is not possible.
+static bool capture_loop(fot_ctx* c, const std::vector<double>& e) {
+  if (c->loop_exec) {
+    cudaGraphExecDestroy(c->loop_exec);
+    c->loop_exec = nullptr;
+    c->loop_key.clear();
+  }
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap = nullptr;
+    return false;
+  }
+  cudaStream_t user = c->stream;
+  const int64_t l0 = c->launches;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+  c->stream = c->cap;
+  loop_body(c, e);
+  c->stream = user;
+  cudaGraph_t g = nullptr;
+  const bool ok = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && g &&
+                  cudaGraphInstantiate(&c->loop_exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  c->loop_kernels = c->launches - l0;
+  c->launches = l0;
+  if (!ok) {
+    cudaGetLastError();
+    c->loop_exec = nullptr;
+    return false;
+  }
+  c->loop_key = e;
+  return true;
+}
+
+// The Sinkhorn loop.  It is replayed as a CUDA graph when kernel timing is off: captured on
+// first use for a schedule (or when at least 16 iterations make the capture pay for itself in
+// the call) and reused while the schedule stays the same.
+static fot_status run_iterations(fot_ctx* c, const double* eps, int n_eps, int units, int iters) {
+  std::vector<double> e((size_t)iters);
+  for (int t = 0; t < iters; ++t) e[(size_t)t] = eps_px(c, eps[n_eps == 1 ? 0 : t], units);
+  const int64_t l0 = c->launches;
+  bool graph = c->ktimer == nullptr && iters > 0;
+  if (graph && !(c->loop_exec && c->loop_key == e)) graph = (iters >= 16 || c->loop_key.empty()) && capture_loop(c, e);
+  if (graph) {
+    cudaEventRecord(c->ev_loop0, c->stream);
+    if (cudaGraphLaunch(c->loop_exec, c->stream) != cudaSuccess) return FOT_ECUDA;
+    cudaEventRecord(c->ev_loop1, c->stream);
+    c->launches += c->loop_kernels;
+    // the host no longer knows which B table the device holds: the next pass rewrites it
+    if (c->tc) tc_begin(c);
+  } else {
+    g_ktimer = c->ktimer;                  // null unless kernel timing is on
+    cudaEventRecord(c->ev_loop0, c->stream);
+    loop_body(c, e);
+    cudaEventRecord(c->ev_loop1, c->stream);
+    g_ktimer = nullptr;
+  }
+  for (int t = 0; t < iters; ++t) c->sched.push_back(e[(size_t)t]);
+  if (iters > 0) c->eps_last = e[(size_t)iters - 1];
   c->loop_passes = c->launches - l0;
   if (iters > 0) c->have_solution = true;
   return check_launch(c);
@@ -527,6 +593,7 @@ fot_status fot_u_update(fot_ctx* c, const float* psi_in, double eps, float* f_ou
   if (!c || bad_ptr(psi_in) || bad_ptr(f_out) || !(eps > 0.0) || !isfinite(eps)) return FOT_EINVAL;
   if (!c->have_problem) return FOT_ESTATE;
   FOT_CUDA(cudaSetDevice(c->device));
+  if (c->tc) tc_begin(c);
   half_step(c, psi_in, c->la, eps, f_out, logsum_out);
   return check_launch(c);
 }
@@ -536,6 +603,7 @@ fot_status fot_v_update(fot_ctx* c, const float* f_in, double eps, float* psi_ou
   if (!c || bad_ptr(f_in) || bad_ptr(psi_out) || !(eps > 0.0) || !isfinite(eps)) return FOT_EINVAL;
   if (!c->have_problem) return FOT_ESTATE;
   FOT_CUDA(cudaSetDevice(c->device));
+  if (c->tc) tc_begin(c);
   half_step(c, f_in, c->lb, eps, psi_out, logsum_out);
   return check_launch(c);
 }

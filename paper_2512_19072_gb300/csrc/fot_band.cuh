@@ -7,7 +7,9 @@
 namespace fot {
 
 // One problem's pass.  plan holds alpha (float), window start and window length (int) per
-// (row, tile of tile_w outputs), n_rows * n_tiles words each, consecutive.
+// (tile of tile_w outputs, row), tile-major: entry (t, r) at t * plan_stride + r, with
+// plan_stride = n_rows rounded up to 128 (a 128-row block's alphas are contiguous), the three
+// arrays n_tiles * plan_stride words each, consecutive.
 struct BandArgs {
   const float* x;      // [n_rows][len] input
   float* plan;
@@ -18,10 +20,25 @@ struct BandArgs {
   unsigned long long* terms;     // [2]: += (row, output, m) triples evaluated on the CUDA cores,
                                  // [0] tilted-GEMM items, [1] exact-window items
   unsigned long long* tc_terms;  // += triples evaluated on the tensor cores
+  // tensor-core pass only (null / 0 otherwise): per 128-row unit (row block, tile) the union
+  // of its rows' windows [ext_lo, ext_hi), reduced by the plan kernel with atomics into the
+  // current buffers; the plan kernel also resets the other pair (the next pass's).  Reset
+  // state: ext_lo = 0x7F7F7F7F, ext_hi = 0.
+  int* ext_lo;
+  int* ext_hi;
+  int* ext_lo_next;
+  int* ext_hi_next;
+  int ext_units;       // entries of each extent array
+  int* ucnt;           // per unit: contributions of a unit split between CTAs (reset to 0)
+  const unsigned char* btab;   // B operand table of this pass (tc_btab_fill)
   float x_scale, c, eps;
   int tile_w;          // outputs per plan tile: 16 (CUDA-core and 16-wide tensor passes) or 64
   int n_rows, len, n_chunks, n_tiles;
+  int plan_stride;     // n_rows rounded up to 128
+  int s_max;           // B table: window stages of the longest possible window (len / 32 up)
   int row_base, plan_base, item_base, cta_base;   // first global work index of each kernel
+  int plan_rows;       // rows of the plan kernel's grid for this problem (n_rows rounded up to 8)
+  alignas(64) unsigned char xmap[128];   // CUtensorMap of x for the tensor-core pass
 };
 
 constexpr int kMaxBatch = 64;
@@ -31,12 +48,19 @@ constexpr int kMaxBatch = 64;
 template <int MAXP>
 struct BandTable {
   int n;                                 // problems
-  int rows, plans, items, ctas;          // totals of the four work kinds
+  int rows, plans, items, ctas;          // totals of the four work kinds (ctas: 128-row units)
+  int plan_row_stride;                   // floats of plan-kernel shared memory per row
+  int plan_tiles;                        // largest n_tiles of the table
+  // tensor-core pass: chunk sums of units split between CTAs ([grid][slot_chunks][128][tile_w]
+  // floats, indexed by the unit's first contributor) and the wait limit of the pipeline barriers
+  float* slots;
+  int slot_chunks;
+  int spin_limit;
   BandArgs p[MAXP];
 };
 
-// problem owning global work index gi of kind WHICH (0 rows, 1 plan CTAs (one per row), 2 band items,
-// 3 tensor CTAs): binary search over the prefix sums (a single problem needs none)
+// problem owning global work index gi of kind WHICH (0 rows, 1 plan rows, 2 band items,
+// 3 tensor-core units): binary search over the prefix sums (a single problem needs none)
 template <int MAXP, int WHICH>
 __device__ __forceinline__ int find_prob(const BandTable<MAXP>& t, int gi) {
   if (MAXP == 1) return 0;
@@ -59,7 +83,7 @@ void band_table_finish(BandTable<MAXP>& t);
 
 // per-(row, tile) plan of every problem
 template <int MAXP>
-void band_prepare(cudaStream_t s, const BandTable<MAXP>& t);
+void band_prepare(cudaStream_t s, BandTable<MAXP>& t);
 
 // the CUDA-core window sums (MODE 0: log-sum output; MODE 1: potential update)
 template <int MODE, int MAXP>
@@ -69,10 +93,17 @@ void band_simt(cudaStream_t s, const BandTable<MAXP>& t);
 int tc_width_for(float c);
 
 // a whole pass on the tensor cores (fot_tc.cu) at tile width tw (every problem of the table
-// must have tc_width_for(c) == tw): finishes the table, plans and launches; tiles outside the
-// tilt bound take CUDA-core sums inside the same kernel, and tw = 0 runs band_simt.  Returns
-// the number of kernels launched.
+// must have tc_width_for(c) == tw and its tensor-core fields set by tc_bind; ctx[q] is problem
+// q's context): finishes the table, writes stale B tables, plans and launches; units outside
+// the tilt bound take CUDA-core sums inside the same kernel, and tw = 0 (or a table the
+// tensor kernel cannot take: rows not 16-byte aligned, too many units) runs band_simt.
+// Returns the number of kernels launched.
 template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw);
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx);
+
+// tensor-core fields of one pass of context c (toggles its unit-extent parity: once per pass)
+void tc_bind(fot_ctx* c, BandArgs& a);
+// start of an API call's sequence of passes on context c (B table rewritten at the first pass)
+void tc_begin(fot_ctx* c);
 
 }  // namespace fot

@@ -57,7 +57,7 @@ template <int MODE, int PATH, bool EXACT_ONLY = false>
 __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int k0, float* sAw) {
   const int lane = threadIdx.x & 31;
   const int h = lane >> 4, i = lane & 15;
-  const size_t np = (size_t)a.n_rows * a.n_tiles;
+  const size_t np = (size_t)a.plan_stride * a.n_tiles;
   const float* __restrict__ p_alpha = a.plan;
   const int* __restrict__ p_lo = reinterpret_cast<const int*>(a.plan + np);
   const int* __restrict__ p_wl = reinterpret_cast<const int*>(a.plan + 2 * np);
@@ -73,7 +73,7 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
   for (int rr = 0; rr < kBR; ++rr) {
     const int r = rh + rr;
     if (r < a.n_rows) {
-      const size_t pi = (size_t)r * a.n_tiles + pt;
+      const size_t pi = (size_t)pt * a.plan_stride + r;
       alpha[rr] = p_alpha[pi];
       lo[rr] = p_lo[pi];
       wl[rr] = p_wl[pi];

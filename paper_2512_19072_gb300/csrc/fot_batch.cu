@@ -24,7 +24,6 @@ namespace fot {
 void set_problem_simt(fot_ctx* c, const float* g, const float* G, float* psi0, float psi0_val);
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 int tc_create(fot_ctx* c);
-unsigned long long* tc_terms_ptr(fot_ctx* c);
 }  // namespace fot
 
 using namespace fot;
@@ -61,6 +60,9 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
   BandTable<kMaxBatch>* tab = new BandTable<kMaxBatch>();
   std::vector<BandArgs> p1(n), p2(n);
   std::vector<int> width(n);
+  std::vector<fot_ctx*> tctx(n);
+  if (use_tc)
+    for (fot_ctx* c : b->ctx) tc_begin(c);
   for (int it = 0; it < iters; ++it) {
     for (int half = 0; half < 2; ++half) {
       for (int q = 0; q < n; ++q) {
@@ -74,7 +76,6 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         a2.y = pout;
         a2.lmarg = half == 0 ? c->la : c->lb;
         a2.logsum = (half == 0 && it == iters - 1) ? c->S_last : nullptr;
-        if (use_tc) a1.tc_terms = a2.tc_terms = tc_terms_ptr(c);
         p1[q] = a1;
         p2[q] = a2;
         width[q] = use_tc ? tc_width_for(a1.c) : -1;
@@ -84,10 +85,15 @@ static void capture_solve(fot_batch* b, cudaStream_t st, const float* const* g, 
         for (int wi = 0; wi < (use_tc ? 4 : 1); ++wi) {
           tab->n = 0;
           for (int q = 0; q < n; ++q)
-            if (width[q] == (use_tc ? kWidths[wi] : -1)) tab->p[tab->n++] = pa[q];
+            if (width[q] == (use_tc ? kWidths[wi] : -1)) {
+              tctx[tab->n] = b->ctx[q];
+              tab->p[tab->n++] = pa[q];
+            }
           if (tab->n == 0) continue;
           if (use_tc) {
-            k += pass == 0 ? tc_pass<0>(st, *tab, kWidths[wi]) : tc_pass<1>(st, *tab, kWidths[wi]);
+            for (int j = 0; j < tab->n; ++j) tc_bind(tctx[j], tab->p[j]);
+            k += pass == 0 ? tc_pass<0>(st, *tab, kWidths[wi], tctx.data())
+                           : tc_pass<1>(st, *tab, kWidths[wi], tctx.data());
           } else {
             band_table_finish(*tab);
             band_prepare(st, *tab);

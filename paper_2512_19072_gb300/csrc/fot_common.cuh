@@ -95,6 +95,12 @@ struct fot_ctx {
   cudaEvent_t ev_loop0 = nullptr, ev_loop1 = nullptr;
   int64_t loop_passes = 0;   // axis-pass launches inside the last loop
   std::vector<double> sched; // eps (px^2) of every iteration since the last fot_solve
+  // the Sinkhorn loop as a CUDA graph (captured on `cap`, replayed on `stream`) and the
+  // per-iteration eps (px^2) it was captured for
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  std::vector<double> loop_key;
+  int64_t loop_kernels = 0;
   // mixed-precision (tensor-core) resources, owned by fot_tc.cu
   void* tc = nullptr;
   fot::KernelTimer* ktimer = nullptr;   // per-kernel-class loop timing, when switched on

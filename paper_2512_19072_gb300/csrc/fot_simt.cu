@@ -140,17 +140,28 @@ static void launch_pass(fot_ctx* c, const PassArgs& p) {
   const int threads = std::min(256, ((p.len + 31) / 32) * 32);
   dim3 grid((p.len + threads - 1) / threads, (p.n_rows + RB - 1) / RB);
   size_t smem = (size_t)p.len * RB * sizeof(float) * (MODE == kMoment ? 2 : 1);
-  static bool configured = false;   // per template instance, per process
-  if (!configured) {
-    cudaFuncSetAttribute(axis_pass_kernel<RB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    configured = true;
-  }
+  // (the dynamic shared-memory limit was raised for this device by simt_configure)
   ktimer_begin(c->stream, kKDense);
   axis_pass_kernel<RB, MODE><<<grid, threads, smem, c->stream>>>(p);
   ktimer_end(c->stream);
   c->launches++;
   c->host_terms += (int64_t)p.n_rows * p.len * p.len;
+}
+
+// Raise the dynamic shared-memory limit of every axis-pass instance on the current device
+// (a per-device function attribute: fot_create calls this with the context's device
+// current, before any stream capture).  The staged rows need len * RB floats (twice that
+// for the moment pass), i.e. more than the 48 KB default once len > 1536.
+cudaError_t simt_configure() {
+  const int lim = 227 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel<8, kLse>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(axis_pass_kernel<8, kLsePot>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(axis_pass_kernel<8, kLseMean>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(axis_pass_kernel<4, kMoment>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
 }
 
 static PassArgs base_args(fot_ctx* c, double eps) {
@@ -438,7 +449,12 @@ void integrate_phase(fot_ctx* c, const float* Dx, const float* Dy, double dx, fl
 // share the array, so calls whose work overlaps on the GPU race on it.
 // ------------------------------------------------------------------------------------
 static __device__ __align__(256) float g_noalloc_scratch[FOT_NOALLOC_MAX_PIXELS];
-static __device__ int g_noalloc_err;   // error word the passes latch into; cleared per call
+// The pass kernels latch a non-finite potential into an error word and skip their work
+// while it is set.  This entry point reads nothing back (it never synchronises), so the word
+// is not reported: it is cleared at the start of every call so that a value latched by an
+// earlier call never makes a later one skip its passes.  A non-finite result shows up as a
+// non-finite value in f_out.
+static __device__ int g_noalloc_err;
 
 namespace {
 constexpr int kNoallocMaxDevices = 64;
@@ -454,9 +470,6 @@ cudaError_t launch_pass_noalloc(const fot::PassArgs& p, cudaStream_t s) {
   const int threads = std::min(256, ((p.len + 31) / 32) * 32);
   dim3 grid((p.len + threads - 1) / threads, (p.n_rows + RB - 1) / RB);
   const size_t smem = (size_t)p.len * RB * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(fot::axis_pass_kernel<RB, MODE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e != cudaSuccess) return e;
   fot::axis_pass_kernel<RB, MODE><<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -474,9 +487,11 @@ extern "C" fot_status fot_u_update_noalloc(const float* psi_in, const float* log
   if (dev < 0 || dev >= kNoallocMaxDevices) return FOT_EUNSUPPORTED;
   NoallocDevice& d = g_noalloc_devices[dev];
   if (!d.ready) {
-    // one-time set-up on this device (current): the symbols' device addresses
+    // one-time set-up on this device (current): the symbols' device addresses and the
+    // shared-memory limit of the two pass kernels (both per-device state)
     if (cudaGetSymbolAddress((void**)&d.scratch, g_noalloc_scratch) != cudaSuccess) return FOT_ECUDA;
     if (cudaGetSymbolAddress((void**)&d.err, g_noalloc_err) != cudaSuccess) return FOT_ECUDA;
+    if (fot::simt_configure() != cudaSuccess) return FOT_ECUDA;
     d.ready = true;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;

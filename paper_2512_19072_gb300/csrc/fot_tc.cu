@@ -1,74 +1,109 @@
 // Tensor-core (tcgen05) form of the banded axis pass.
 //
-// The window sums of the banded pass (fot_band.cu, steps 3-4) are a GEMM:
+// The window sums of the banded pass (fot_band.cu, steps 3-4) are a GEMM.  A unit is a
+// 128-row block of the input x and a tile of TN consecutive outputs o = kc + kap around the
+// tile centre kc.  The plan kernel gives every row r its offset alpha_r (at most the largest
+// term at kc) and its window, and the union of the 128 windows [lo, lo + W) (W a multiple of
+// 32).  Indexing the union window from its own start (m = lo + m'),
 //     C[r][kap] = sum_{m' < W} A[r][m'] B[m'][kap],
-//     A[r][m'] = 2^(x_r[lo_r + m'] - (kc - lo_r - m')^2 c - alpha_r)   (<= 1, per row)
-//     B[m'][kap] = 2^(2 kap (m' - W/2) c - kap^2 c)                     (same for all rows)
-// after which y[kc + kap][r] = alpha_r + 2 kap (lo_r + W/2 - kc) c + log2 C[r][kap] (the
-// per-row max-offsets of Sec. 3.1's Toeplitz contraction, plus the tilt).  One CTA computes
-// a 128-row x TN-output tile (TN = 16, 32 or 64) with tcgen05.mma (M = 128, N = TN, K = 16
-// per instruction), the FP32 accumulator in tensor memory.  A wider tile shares one A operand
-// (one exponential per row and window position) between more outputs; the host picks the
-// widest one whose tilt bound the problem's eps allows.
+//     A[r][m'] = 2^(x_r[lo + m'] - (kc - lo - m')^2 c - alpha_r)      (per row)
+//     B[m'][kap] = 2^(2 kap (m' - W/2) c - kap^2 c)                    (the same for all rows)
+// and y[kc + kap][r] = alpha_r + 2 kap (lo + W/2 - kc) c + log2 C[r][kap]: the per-row
+// max-offsets of Sec. 3.1's Toeplitz contraction plus the tilt of the tile.  The union window
+// holds every row's own window, so each row's sum covers at least its provable window; the
+// extra positions only add exact (small) terms.
 //
-// Warp roles: eight producer warps generate the operands of each 32-position stage in shared
-// memory (canonical no-swizzle K-major layout) and arrive on the stage's "full" mbarrier; one
-// more warp owns the tensor memory and issues the stage's MMAs once all producers have
-// arrived, committing to the stage's "empty" mbarrier, which the producers wait on before
-// reusing it (a ring of four stages).  A last commit signals the epilogue, in which the producers read
-// the accumulator (the potential-update pass prefetches its marginals during the last MMAs).
+// One persistent CTA per SM.  The stages (32 window positions each) of all units of the pass
+// are laid end to end and every CTA takes an equal contiguous share of them (stream-K).  A
+// unit is accumulated in chunks of kChunk stages, each in a fresh accumulator, and the chunk
+// sums are added in chunk order; a CTA takes the chunks that start in its share.  A unit whose
+// chunks fall into several shares is split: each contributor writes its chunk sums to global
+// slots and the last one to arrive adds them in chunk order and writes the outputs.  The
+// arithmetic of every output is thus the same whatever the split (and whatever else shares the
+// launch, e.g. the other problems of a batch): results do not depend on the grid.
 //
-// Precision: each operand is split into two BF16 parts, v = hi + lo (hi = bf16(v),
-// lo = bf16(v - hi)), and the product is accumulated as hi*hi + hi*lo + lo*hi (three MMAs):
-// about 2^-16 relative per product instead of 2^-8, FP32 accumulation.  The epilogue takes
-// log2 of the accumulator with the MUFU unit (about 2^-22 absolute), far below that.
+// Warp roles (704 threads):
+//  * warp 16, one lane (TMA): per stage, the 128 x 32 FP32 tile of x by a 2-D tensor copy
+//    (128-byte swizzle), at a unit's first stage also the 128 row offsets alpha (a 1-D bulk
+//    copy, once for the producers and once for the epilogue), and the stage's B operand (a
+//    1-D bulk copy from the pass's B table).
+//  * warps 0-15 (producers): thread (row ar, quarter aq) turns its 8 window positions into A,
+//    split into two BF16 parts (v = hi + lo), stored in the canonical K-major core-matrix
+//    layout.
+//  * warp 17, one lane (MMA): per 16-position K step two tcgen05.mma (kind::f16, M = 128):
+//    A_hi x [B_hi | B_lo] (N = 2 TN) and A_lo x B_hi (N = TN) into an FP32 accumulator in
+//    tensor memory, so that hi*hi + hi*lo + lo*hi is accumulated (about 2^-16 relative per
+//    product instead of 2^-8); two accumulators alternate between consecutive units.
+//  * warps 18-21 (epilogue): read the accumulator (tcgen05.ld), add its two halves, take log2
+//    (MUFU lg2), add the offsets; the potential-update pass also applies
+//    f = eps (log a - S) with log a prefetched into shared memory.
+// Every barrier wait is bounded: on time-out the kernel latches FOT_ETIMEOUT, all roles leave
+// their loops, the copies and MMAs in flight are waited for (again bounded) and the tensor
+// memory is freed.
 //
-// A CTA uses the tensor cores only when the tilt bound holds for the common window length W
-// of its 128 rows: |kap| W c <= 48 with |kap| <= TN / 2.  Then every output's largest term has
-// A >= 2^-96, and the A values that flush below 2^-126 add less than W 2^-30 relative: below
-// the 2^-16 of the split-BF16 products.  Otherwise its producer warps compute the tile with the
-// CUDA-core window sums of the banded pass (16 rows each; for a wider tile the exact window
-// sums over the tile's window, which covers the windows of its 16-wide parts).  Every mbarrier
-// wait is bounded: on time-out the kernel latches FOT_ETIMEOUT, stops issuing, waits (again
-// bounded) for the MMAs in flight, frees its tensor memory and returns.
+// A unit takes the tensor cores when its tilt bound holds: |kap| W c <= 48 with |kap| <= TN/2
+// (and kap^2 c <= 32).  The largest term of every output then has A >= 2^-96 (alpha is at most
+// the largest term at kc), and the A values that flush below 2^-126 add less than W 2^-30
+// relative.  Other units (and units whose rows carry no mass) are summed on the CUDA cores by
+// the producer warps after the tensor work (the banded pass's window sums, 16 rows per warp).
 #include "fot_band_item.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <stdlib.h>
 
+#include <algorithm>
 #include <new>
 
 namespace fot {
 
 namespace {
 
-constexpr int kTM = 128;            // rows per CTA (MMA M, TMEM lanes)
-constexpr int kKC = 32;             // window positions per pipeline stage
-constexpr int kStages = 4;          // operand stages in flight
-constexpr int kPH = kKC / 2;        // window positions per producer thread and stage
-constexpr int kGroupBytes = (kKC / 8) * 128;   // bytes between 8-row core-matrix groups
-constexpr int kRouteKC = 64;        // window rounding of the host's tile-width estimate
-constexpr int kProducerWarps = 8;   // operand producers (256 threads)
-constexpr int kThreadsTC = kProducerWarps * 32 + 32;   // + the MMA-issuing warp
+constexpr int kTM = 128;                 // rows per unit (MMA M, TMEM lanes)
+constexpr int kKC = 32;                  // window positions per stage
+constexpr int kXStages = 4;              // x tiles in flight
+constexpr int kOpStages = 4;             // operand stages in flight
+constexpr int kAccBufs = 2;              // tensor-memory accumulators
+constexpr int kEpiAlpha = 4;             // epilogue copies of alpha in flight
+constexpr int kProdWarps = 16;
+constexpr int kProd = kProdWarps * 32;   // 512 producer threads
+constexpr int kTmaWarp = 16, kMmaWarp = 17, kEpiWarp0 = 18, kEpiWarps = 4;
+constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;   // 704
+constexpr int kWarps = kThreads / 32;
+constexpr int kEpi = kEpiWarps * 32;     // 128 epilogue threads, one per accumulator row
+constexpr int kXBytes = kTM * kKC * 4;   // 16 KB x tile
+constexpr int kAlphaBytes = kTM * 4;     // 512 B of offsets
+constexpr int kABytes = kTM * kKC * 2;   // 8 KB per BF16 part of A
+constexpr int kGroupBytes = (kKC / 8) * 128;   // 512 B between 8-row core-matrix groups
 constexpr float kTiltMaxTC = 48.f;
-constexpr int kSpin = 1 << 20;      // bounded mbarrier polls
+constexpr int kMaxPieces = 128;          // units one CTA's share may touch
+constexpr int kChunk = 4;                // stages per accumulation chunk
+constexpr int kMaxDecl = 64;             // CUDA-core units per CTA
+constexpr int kUnitsPerThread = 8;       // units each thread holds during the set-up scan
+constexpr int kSpinDefault = 1 << 20;    // bounded mbarrier polls
+constexpr int kRouteKC = 64;             // window rounding of the host's tile-width estimate
 
-// shared-memory layout of one stage (bytes): A_hi, A_lo (128 x 32 bf16 each), B_hi, B_lo
-// (TN x 32 bf16 each), in 8 x 16-byte core matrices: core (g, kg) at g * 512 + kg * 128.
-constexpr int kABytes = kTM * kKC * 2;   // 8192
+// dynamic shared memory (bytes from a 1024-aligned base): the x ring, the producers' alpha per
+// x slot, the epilogue's alpha ring, the log-marginal prefetch, the operand ring
 template <int TN> struct TcShape {
-  static constexpr int kBBytes = TN * kKC * 2;
-  static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-  static constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // the ring + slack
-  static constexpr uint32_t kTmemCols = TN < 32 ? 32 : TN;    // power of two >= 32
+  static constexpr int kBBytes = 2 * TN * kKC * 2;          // B_hi rows, then B_lo rows
+  static constexpr int kOpBytes = 2 * kABytes + kBBytes;
+  static constexpr int kXAlphaOff = kXStages * kXBytes;
+  static constexpr int kEAlphaOff = kXAlphaOff + kXStages * kAlphaBytes;
+  static constexpr int kLmOff = kEAlphaOff + kEpiAlpha * kAlphaBytes;
+  static constexpr int kOpOff = kLmOff + TN * kTM * 4;
+  static constexpr int kSmemBytes = kOpOff + kOpStages * kOpBytes + 1024;
+  // 2 accumulators of 2TN columns, then the TN-column running sum of a unit's chunks
+  static constexpr uint32_t kTmemCols = 5 * TN <= 32 ? 32 : 5 * TN <= 64 ? 64 : 5 * TN <= 128 ? 128 : 5 * TN <= 256 ? 256 : 512;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// tcgen05 shared-memory matrix descriptor, no swizzle, K-major:
-// start address, leading (K-direction core-matrix) byte offset, stride (M/N-direction
-// 8-row group) byte offset, fixed version bits 46-48 = 0b001.
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major: start address, leading
+// (K-direction core-matrix) byte offset, stride (M/N-direction 8-row group) byte offset,
+// fixed version bits 46-48 = 0b001.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
@@ -104,6 +139,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(mbar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -113,17 +152,51 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false (and FOT_ETIMEOUT latched) if the phase never completes
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int* err) {
-  for (int i = 0; i < kSpin; ++i)
+// Bounded wait.  Returns false when another role has aborted the CTA, or when `limit` polls
+// pass (then FOT_ETIMEOUT is latched and the CTA aborted).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit, int* err,
+                                          volatile int* abort) {
+  for (int i = 0; i < limit; ++i) {
     if (mbar_try(mbar, parity)) return true;
+    if ((i & 31) == 31 && *abort) return false;
+  }
   raise_error(err, FOT_ETIMEOUT);
+  *abort = 1;
   return false;
 }
 
+// bounded wait that ignores the abort flag (the drain after an abort)
+__device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity) {
+  for (int i = 0; i < kSpinDefault; ++i)
+    if (mbar_try(mbar, parity)) return;
+}
+
+// AND of pred over the 128 epilogue threads (named barrier 2): a decision they all take alike
+__device__ __forceinline__ bool epi_all(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r) : "r"((uint32_t)pred), "r"(kEpi) : "memory");
+  return r != 0;
+}
+
+// 2-D tensor copy of one box (x tile) into shared memory, completing on mbar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int c0, int c1, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(dst), "l"(tmap), "r"(c0), "r"(c1), "r"(mbar) : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
 // split 8 consecutive values into hi / lo BF16 parts (hi = round(v), lo = round(v - hi)) and
-// store one 16-byte row of a core matrix for each (plain shared-memory stores; the caller
-// fences them for the tensor core's async proxy)
+// store one 16-byte core-matrix row of each
 __device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p, unsigned char* lo_p) {
   uint32_t hw[4], lw[4];
 #pragma unroll
@@ -138,278 +211,429 @@ __device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p
   *reinterpret_cast<uint4*>(lo_p) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
-// CUDA-core window sums of a declined tile (kept out of line: rarely run, and large)
+// the CTA holding stage x of the pass when S stages are shared out over C CTAs (CTA k takes
+// [k S / C, (k + 1) S / C))
+__device__ __forceinline__ int cta_of(long long x, long long S, int C) {
+  return (int)(((x + 1) * C - 1) / S);
+}
+__device__ __forceinline__ long long share_start(int k, long long S, int C) { return (long long)k * S / C; }
+
+// what a unit needs: its stage count when it takes the tensor cores (0 otherwise), whether it
+// takes the CUDA-core sums instead, its union window start
+template <int TN, int MAXP>
+__device__ __forceinline__ void unit_info(const BandTable<MAXP>& tab, int u, int& S, int& decl, int& lo) {
+  const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, u)];
+  const int lu = u - a.cta_base;
+  lo = a.ext_lo[lu];
+  const int hi = a.ext_hi[lu];
+  const int W = hi > lo ? (hi - lo + kKC - 1) / kKC * kKC : 0;
+  const float kmax = (float)(TN / 2);
+  const bool latched = error_latched(a.err);
+  const bool take = !latched && W > 0 && kmax * (float)W * a.c <= kTiltMaxTC && kmax * kmax * a.c <= 32.f;
+  S = take ? W / kKC : 0;
+  decl = (!latched && !take) ? 1 : 0;
+}
+
+// CUDA-core window sums of a unit outside the tensor path: 16-row items, the tile's 16-wide
+// parts (for a wider tile the exact window sums over the tile's window)
 template <int MODE, int TN>
-__device__ __noinline__ void tc_declined_tile(const BandArgs& a, int rw, int tile, int k0, float* sAw) {
-  if (TN == kBT) {
-    band_item<MODE, 0>(a, rw, tile, k0, sAw);
-    band_item<MODE, 1>(a, rw, tile, k0, sAw);
-  } else {
-    for (int q = 0; q < TN / kBT && k0 + q * kBT < a.len; ++q)
-      band_item<MODE, 1, true>(a, rw, tile, k0 + q * kBT, sAw);
+__device__ __noinline__ void tc_cuda_core_unit(const BandArgs& a, int r0, int tile, int k0, int warp, float* sAw) {
+  for (int it = warp; it < (kTM / (2 * kBR)) * (TN / kBT); it += kProdWarps) {
+    const int rw = r0 + (it % (kTM / (2 * kBR))) * 2 * kBR;
+    const int kq = k0 + (it / (kTM / (2 * kBR))) * kBT;
+    if (rw >= a.n_rows || kq >= a.len) continue;           // warp-uniform
+    if (TN == kBT) {
+      band_item<MODE, 0>(a, rw, tile, kq, sAw);
+      band_item<MODE, 1>(a, rw, tile, kq, sAw);
+    } else {
+      band_item<MODE, 1, true>(a, rw, tile, kq, sAw);
+    }
   }
 }
 
 template <int MODE, int TN, int MAXP>
-__global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
-  constexpr int kTN = TN;
-  constexpr int kStageBytes = TcShape<TN>::kStageBytes;
-  constexpr int kBBytes = TcShape<TN>::kBBytes;
-  constexpr uint32_t kTmemCols = TcShape<TN>::kTmemCols;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full[kStages], empty[kStages], done;
-  __shared__ uint32_t tmem_base_sh;
-  __shared__ int s_wm[kTM / 32], s_err;
-  const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, (int)blockIdx.x)];
+__global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+  using Sh = TcShape<TN>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t xfull[kXStages], xempty[kXStages];
+  __shared__ uint64_t opfull[kOpStages], opempty[kOpStages], bfull[kOpStages];
+  __shared__ uint64_t accfull[kAccBufs], accempty[kAccBufs];
+  __shared__ uint64_t eafull[kEpiAlpha], eaempty[kEpiAlpha];
+  __shared__ uint64_t drain;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort, s_np, s_nd, s_first, s_last;
+  __shared__ int4 s_piece[kMaxPieces];   // unit, first stage of the unit in the pass, stages, lo
+  __shared__ int s_decl[kMaxDecl];
+  __shared__ long long s_wsum[kWarps][2];
+
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lb = (int)blockIdx.x - a.cta_base;
-  const int blk = lb / a.n_tiles, tile = lb % a.n_tiles;
-  const int r0 = blk * kTM;
-  const int k0 = tile * kTN, kc = k0 + kTN / 2;
-  const int k1 = min(k0 + kTN, a.len) - 1;
-  const float c = a.c, sc = a.x_scale;
-  const bool producer = warp < kProducerWarps;
+  const int C = (int)gridDim.x, cta = (int)blockIdx.x;
+  const int spin = tab.spin_limit;
+  volatile int* abort_flag = &s_abort;
+  int* err0 = tab.p[0].err;
 
-  // producer roles: A row r0 + ar (ar = tid % 128, which is also the accumulator row, i.e.
-  // the tensor-memory lane 32 (warp % 4) + lane, that this thread reads in the epilogue),
-  // half ah = tid / 128 (16 window positions each); B: core rows q = tid, tid + 256, ... of
-  // TN outputs x 8 groups of 8 positions.  Both threads of a row read its plan entry straight
-  // from global memory and start the loads of its first window chunk before any barrier, so
-  // that the CTA waits out one memory latency before its first stage instead of three.
-  const int ar = tid & (kTM - 1), ah = (tid >> 7) & 1;
-  float a_alpha = -INFINITY;
-  int a_lo = 0, a_wl = 0;
-  if (producer && r0 + ar < a.n_rows) {
-    const size_t np = (size_t)a.n_rows * a.n_tiles;
-    const size_t pi = (size_t)(r0 + ar) * a.n_tiles + tile;
-    a_alpha = a.plan[pi];
-    a_lo = reinterpret_cast<const int*>(a.plan + np)[pi];
-    a_wl = reinterpret_cast<const int*>(a.plan + 2 * np)[pi];
+  if (tid == 0) {
+    s_abort = 0;
+    s_np = 0;
+    s_nd = 0;
+    s_first = 0x7fffffff;
   }
-  // window positions m' >= the row's own window length hold only terms below 2^-kCut of every
-  // output of the tile (the provable window): their A values are written as zeros, with no
-  // load and no exponential (rows with short windows cost little in a long tile)
-  const float* xr = a.x + (size_t)min(r0 + ar, a.n_rows - 1) * a.len;
-  // x of the next chunk, prefetched: 16 consecutive window positions of row ar.  lo and each
-  // chunk start are multiples of 32, so the float4 loads are aligned; positions at or
-  // beyond len read -inf (the kernel skips rows without mass).
-  const bool a_live = producer && a_alpha != -INFINITY;
-  // the 16-byte vector load needs the row base aligned too: x + row * len is 16-byte aligned
-  // only when row * len is a multiple of 4 (window starts are multiples of 32)
-  const bool vec_ok = (reinterpret_cast<uintptr_t>(xr) & 15u) == 0;
-  float4 xq[kPH / 4];
-  auto load_x = [&](int m0) {
-    if (m0 + ah * kPH >= a_wl) return;                  // outside the row's window
-    const int mb = a_lo + m0 + ah * kPH;
-#pragma unroll
-    for (int q = 0; q < kPH / 4; ++q) {
-      const int m = mb + 4 * q;
-      if (a_live && vec_ok && m + 3 < a.len) {
-        xq[q] = __ldg(reinterpret_cast<const float4*>(xr + m));
-      } else {
-        xq[q].x = (a_live && m < a.len) ? xr[m] : -INFINITY;
-        xq[q].y = (a_live && m + 1 < a.len) ? xr[m + 1] : -INFINITY;
-        xq[q].z = (a_live && m + 2 < a.len) ? xr[m + 2] : -INFINITY;
-        xq[q].w = (a_live && m + 3 < a.len) ? xr[m + 3] : -INFINITY;
-      }
-    }
-  };
-  if (producer) load_x(0);                  // in flight while the CTA sets up
-
-  // the common window length of the 128 rows: warps 0-3 hold one thread per row
-  int wm = a_wl;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, off));
-  if (lane == 0 && warp < kTM / 32) s_wm[warp] = wm;
-  if (tid == 0) s_err = error_latched(a.err) ? 1 : 0;   // one read: the exit is CTA-uniform
-
-  // the MMA warp owns the tensor memory (128 x TN FP32 accumulator) and the barriers:
-  // full[s] (256 producer arrivals: stage s written), empty[s] (the commit of the MMAs that
-  // read stage s), done (the commit after the last chunk)
-  if (warp == kProducerWarps) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base_sh)), "r"(kTmemCols) : "memory");
+                 :: "r"(smem_u32(&s_tmem)), "r"(Sh::kTmemCols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    if (lane == 0) {
-      for (int i = 0; i < kStages; ++i) {
-        mbar_init(smem_u32(&full[i]), kProducerWarps * 32);
-        mbar_init(smem_u32(&empty[i]), 1);
+  }
+  if (warp == kTmaWarp && lane == 0) {
+    for (int i = 0; i < kXStages; ++i) {
+      mbar_init(smem_u32(&xfull[i]), 1);
+      mbar_init(smem_u32(&xempty[i]), kProd);
+    }
+    for (int i = 0; i < kOpStages; ++i) {
+      mbar_init(smem_u32(&opfull[i]), kProd);
+      mbar_init(smem_u32(&opempty[i]), 1);
+      mbar_init(smem_u32(&bfull[i]), 1);
+    }
+    for (int i = 0; i < kAccBufs; ++i) {
+      mbar_init(smem_u32(&accfull[i]), 1);
+      mbar_init(smem_u32(&accempty[i]), kEpi);
+    }
+    for (int i = 0; i < kEpiAlpha; ++i) {
+      mbar_init(smem_u32(&eafull[i]), 1);
+      mbar_init(smem_u32(&eaempty[i]), kEpi);
+    }
+    mbar_init(smem_u32(&drain), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+
+  // ---- set-up: the stage counts of all units, their prefix sums, this CTA's share -------------
+  const int U = tab.ctas;
+  const int per = (U + kThreads - 1) / kThreads;          // <= kUnitsPerThread (host check)
+  const int u0 = min(U, tid * per), u1 = min(U, u0 + per);
+  int uS[kUnitsPerThread], uD[kUnitsPerThread], uL[kUnitsPerThread];
+  long long my_s = 0, my_t = 0;                           // stages; tensor units | CUDA-core units << 32
+#pragma unroll
+  for (int i = 0; i < kUnitsPerThread; ++i) {
+    uS[i] = 0;
+    uD[i] = 0;
+    uL[i] = 0;
+    if (u0 + i < u1) {
+      unit_info<TN>(tab, u0 + i, uS[i], uD[i], uL[i]);
+      my_s += uS[i];
+      my_t += (uS[i] > 0 ? 1ll : 0ll) + ((long long)uD[i] << 32);
+    }
+  }
+  // block-wide exclusive scan of (stages, counts) in unit order
+  long long inc_s = my_s, inc_t = my_t;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long vs = __shfl_up_sync(0xffffffffu, inc_s, d);
+    const long long vt = __shfl_up_sync(0xffffffffu, inc_t, d);
+    if (lane >= d) {
+      inc_s += vs;
+      inc_t += vt;
+    }
+  }
+  if (lane == 31) {
+    s_wsum[warp][0] = inc_s;
+    s_wsum[warp][1] = inc_t;
+  }
+  __syncthreads();
+  long long base_s = inc_s - my_s, base_t = inc_t - my_t, tot_s = 0, tot_t = 0;
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) {
+      base_s += s_wsum[w][0];
+      base_t += s_wsum[w][1];
+    }
+    tot_s += s_wsum[w][0];
+    tot_t += s_wsum[w][1];
+  }
+  const long long S_tot = tot_s;
+  const long long sb = S_tot > 0 ? share_start(cta, S_tot, C) : 0;
+  const long long se = S_tot > 0 ? share_start(cta + 1, S_tot, C) : 0;
+  // this CTA takes the chunks of unit u that start in [sb, se): chunks [jlo, jhi)
+  auto chunks_here = [&](long long P, int S, int& jlo, int& jhi) {
+    const int nc = (S + kChunk - 1) / kChunk;
+    jlo = sb > P ? (int)min((long long)nc, (sb - P + kChunk - 1) / kChunk) : 0;
+    jhi = se > P ? (int)min((long long)nc, (se - P + kChunk - 1) / kChunk) : 0;
+  };
+  {
+    long long P = base_s, R = base_t & 0xffffffffll;
+#pragma unroll
+    for (int i = 0; i < kUnitsPerThread; ++i) {
+      if (uS[i] > 0) {
+        int jlo, jhi;
+        chunks_here(P, uS[i], jlo, jhi);
+        if (jlo < jhi) atomicMin(&s_first, (int)R);
       }
-      mbar_init(smem_u32(&done), 1);
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      P += uS[i];
+      R += uS[i] > 0 ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  {
+    long long P = base_s, R = base_t & 0xffffffffll, D = base_t >> 32;
+#pragma unroll
+    for (int i = 0; i < kUnitsPerThread; ++i) {
+      if (uS[i] > 0) {
+        int jlo, jhi;
+        chunks_here(P, uS[i], jlo, jhi);
+        if (jlo < jhi) {
+          const int idx = (int)(R - s_first);
+          if (idx >= 0 && idx < kMaxPieces) {
+            s_piece[idx] = make_int4(u0 + i, (int)P, uS[i], uL[i]);
+            atomicMax(&s_np, idx + 1);
+          } else {
+            raise_error(err0, FOT_EUNSUPPORTED);
+          }
+        }
+      }
+      if (uD[i] && (int)(D % C) == cta) {
+        const int idx = (int)(D / C);
+        if (idx < kMaxDecl) {
+          s_decl[idx] = u0 + i;
+          atomicMax(&s_nd, idx + 1);
+        } else {
+          raise_error(err0, FOT_EUNSUPPORTED);
+        }
+      }
+      P += uS[i];
+      R += uS[i] > 0 ? 1 : 0;
+      D += uD[i];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int wmax = max(max(s_wm[0], s_wm[1]), max(s_wm[2], s_wm[3]));
-  const int W = ((wmax + kKC - 1) / kKC) * kKC;
-  const float kmax = (float)(kTN / 2);
-  const bool take = wmax > 0 && kmax * (float)W * c <= kTiltMaxTC && kmax * kmax * c <= 32.f;
-  if (s_err || !take) {                                 // CTA-uniform
-    if (warp == kProducerWarps)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base_sh),
-                   "r"(kTmemCols) : "memory");
-    if (s_err) return;
-    const int rw = r0 + warp * 2 * kBR;                 // producer warp w: rows rw .. rw + 15
-    if (warp < kProducerWarps && rw < a.n_rows)
-      tc_declined_tile<MODE, TN>(a, rw, tile, k0, reinterpret_cast<float*>(smem) + warp * 2 * kSA);
-    return;
-  }
-  if (tid == 0) atomicAdd(a.tc_terms, (unsigned long long)W * kTN * kTM);
+  const uint32_t tmem = s_tmem;
+  const int np = s_np, nd = s_nd;
 
-  const uint32_t sbase = smem_u32(smem);
-  const float halfW = 0.5f * (float)W;
-  const int nchunk = W / kKC;
-  const uint32_t tmem_d = tmem_base_sh;
-  bool ok = true;
+  // piece i: unit, its chunks [jlo, jhi) here (stages [b, e)), whether it is split, and the
+  // first contributor (whose index names the split unit's slots)
+  struct Piece {
+    const BandArgs* a;
+    int lu, r0, tile, k0, kc, lo, S, nc, jlo, jhi, b, e, P, ca, cb;
+    bool split;
+  };
+  auto piece = [&](int i) {
+    const int4 q = s_piece[i];
+    Piece p;
+    p.a = &tab.p[find_prob<MAXP, 3>(tab, q.x)];
+    p.lu = q.x - p.a->cta_base;
+    p.r0 = (p.lu / p.a->n_tiles) * kTM;
+    p.tile = p.lu % p.a->n_tiles;
+    p.k0 = p.tile * TN;
+    p.kc = p.k0 + TN / 2;
+    p.lo = q.w;
+    p.S = q.z;
+    p.P = q.y;
+    p.nc = (q.z + kChunk - 1) / kChunk;
+    chunks_here(q.y, q.z, p.jlo, p.jhi);
+    p.b = p.jlo * kChunk;
+    p.e = min(p.jhi * kChunk, p.S);
+    p.ca = cta_of(q.y, S_tot, C);
+    p.cb = cta_of((long long)q.y + (long long)(p.nc - 1) * kChunk, S_tot, C);
+    p.split = p.ca != p.cb;
+    return p;
+  };
 
-  if (!producer) {
-    // MMA warp: lane 0 issues each stage's MMAs once its 256 producers have arrived
+  unsigned char* const xring = smem;
+  unsigned char* const xalpha = smem + Sh::kXAlphaOff;
+  unsigned char* const ealpha = smem + Sh::kEAlphaOff;
+  float* const s_lm = reinterpret_cast<float*>(smem + Sh::kLmOff);
+  unsigned char* const opring = smem + Sh::kOpOff;
+  int issued_x = 0, issued_o = 0, issued_ea = 0, issued_mma = 0;   // for the drain after an abort
+
+  if (warp == kTmaWarp) {
+    // ---------------------------------------------------------------- TMA issue (one lane)
     if (lane == 0) {
-      const uint32_t idesc = instr_desc(kTM, kTN);
-      for (int ch = 0; ch < nchunk; ++ch) {
-        const int s = ch % kStages;
-        if (!mbar_wait(smem_u32(&full[s]), (ch / kStages) & 1, a.err)) {
-          ok = false;
-          break;
+      int xi = 0, oi = 0;
+      bool ok = true;
+      for (int i = 0; i < np && ok; ++i) {
+        const Piece p = piece(i);
+        const BandArgs& a = *p.a;
+        const float* alpha_src = a.plan + (size_t)p.tile * a.plan_stride + p.r0;
+        for (int ch = p.b; ch < p.e && ok; ++ch) {
+          const int s = xi % kXStages;
+          if (xi >= kXStages && !(ok = mbar_wait(smem_u32(&xempty[s]), ((xi / kXStages) - 1) & 1, spin, a.err, abort_flag))) break;
+          const bool first = ch == p.b;
+          mbar_expect_tx(smem_u32(&xfull[s]), kXBytes + (first ? kAlphaBytes : 0));
+          tma_load_2d(smem_u32(xring + s * kXBytes), a.xmap, p.lo + ch * kKC, p.r0, smem_u32(&xfull[s]));
+          if (first) bulk_load(smem_u32(xalpha + s * kAlphaBytes), alpha_src, kAlphaBytes, smem_u32(&xfull[s]));
+          ++xi;
+          issued_x = xi;
+          if (first) {
+            const int ea = i % kEpiAlpha;
+            if (i >= kEpiAlpha && !(ok = mbar_wait(smem_u32(&eaempty[ea]), ((i / kEpiAlpha) - 1) & 1, spin, a.err, abort_flag))) break;
+            mbar_expect_tx(smem_u32(&eafull[ea]), kAlphaBytes);
+            bulk_load(smem_u32(ealpha + ea * kAlphaBytes), alpha_src, kAlphaBytes, smem_u32(&eafull[ea]));
+            issued_ea = i + 1;
+          }
+          const int so = oi % kOpStages;
+          if (oi >= kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / kOpStages) - 1) & 1, spin, a.err, abort_flag))) break;
+          mbar_expect_tx(smem_u32(&bfull[so]), Sh::kBBytes);
+          const int e_idx = 2 * ch - p.S + a.s_max;
+          bulk_load(smem_u32(opring + so * Sh::kOpBytes + 2 * kABytes), a.btab + (size_t)e_idx * Sh::kBBytes,
+                    Sh::kBBytes, smem_u32(&bfull[so]));
+          ++oi;
+          issued_o = oi;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = sbase + s * kStageBytes;
-        const uint32_t sAhi = st, sAlo = st + kABytes, sBhi = st + 2 * kABytes, sBlo = sBhi + kBBytes;
-#pragma unroll
-        for (int ks = 0; ks < kKC / 16; ++ks) {
-          const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, kGroupBytes);
-          const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, kGroupBytes);
-          const uint64_t dBh = smem_desc(sBhi + ks * 256, 128, kGroupBytes);
-          const uint64_t dBl = smem_desc(sBlo + ks * 256, 128, kGroupBytes);
-          mma_bf16(tmem_d, dAh, dBh, idesc, (ch > 0 || ks > 0) ? 1u : 0u);
-          mma_bf16(tmem_d, dAh, dBl, idesc, 1u);
-          mma_bf16(tmem_d, dAl, dBh, idesc, 1u);
-        }
-        mma_commit(smem_u32(&empty[s]));
       }
-      // arrives when every MMA issued above has completed; the producers wait on it before
-      // reading the accumulator, and this thread before the tensor memory is released
-      mma_commit(smem_u32(&done));
-      ok = mbar_wait(smem_u32(&done), 0, a.err) && ok;
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------------- MMA issue (one lane)
+    if (lane == 0) {
+      const uint32_t idesc1 = instr_desc(kTM, 2 * TN), idesc2 = instr_desc(kTM, TN);
+      int oi = 0, ai = 0;
+      bool ok = true;
+      for (int i = 0; i < np && ok; ++i) {
+        const Piece p = piece(i);
+        for (int j = p.jlo; j < p.jhi && ok; ++j) {
+          // chunk j: a fresh accumulator over its stages
+          const int ab = ai % kAccBufs;
+          if (ai >= kAccBufs && !(ok = mbar_wait(smem_u32(&accempty[ab]), ((ai / kAccBufs) - 1) & 1, spin, p.a->err, abort_flag))) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dcol = tmem + (uint32_t)(ab * 2 * TN);
+          const int s0 = j * kChunk, s1 = min(s0 + kChunk, p.S);
+          for (int ch = s0; ch < s1; ++ch) {
+            const int so = oi % kOpStages;
+            const uint32_t par = (oi / kOpStages) & 1;
+            if (!(ok = mbar_wait(smem_u32(&opfull[so]), par, spin, p.a->err, abort_flag))) break;
+            if (!(ok = mbar_wait(smem_u32(&bfull[so]), par, spin, p.a->err, abort_flag))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(opring + so * Sh::kOpBytes);
+            const uint32_t sAhi = st, sAlo = st + kABytes, sB = st + 2 * kABytes;
+#pragma unroll
+            for (int ks = 0; ks < kKC / 16; ++ks) {
+              const uint64_t dAh = smem_desc(sAhi + ks * 256, 128, kGroupBytes);
+              const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, kGroupBytes);
+              const uint64_t dB = smem_desc(sB + ks * 256, 128, kGroupBytes);
+              mma_bf16(dcol, dAh, dB, idesc1, (ch > s0 || ks > 0) ? 1u : 0u);   // hi x [B_hi | B_lo]
+              mma_bf16(dcol, dAl, dB, idesc2, 1u);                               // lo x B_hi
+            }
+            mma_commit(smem_u32(&opempty[so]));
+            issued_mma = 1;
+            ++oi;
+          }
+          if (!ok) break;
+          mma_commit(smem_u32(&accfull[ab]));
+          ++ai;
+        }
+      }
     }
     __syncwarp();
-  } else {
-    for (int ch = 0; ch < nchunk; ++ch) {
-      const int s = ch % kStages;
-      // stage free again: the MMAs of chunk ch - kStages (its previous use) have completed
-      if (ch >= kStages && !mbar_wait(smem_u32(&empty[s]), ((ch - kStages) / kStages) & 1, a.err)) {
-        ok = false;
-        break;
-      }
-      unsigned char* const stp = smem + s * kStageBytes;
-      const int m0 = ch * kKC;
-      float xv[kPH];
-#pragma unroll
-      for (int q = 0; q < kPH / 4; ++q) {
-        xv[4 * q] = xq[q].x;
-        xv[4 * q + 1] = xq[q].y;
-        xv[4 * q + 2] = xq[q].z;
-        xv[4 * q + 3] = xq[q].w;
-      }
-      if (ch + 1 < nchunk) load_x(m0 + kKC);
-      // A: 16 consecutive window positions of row ar -> 2 core-matrix rows of 8 values
-      const float dbase = (float)(kc - (a_lo + m0 + ah * kPH));
-      if (!a_live || m0 + ah * kPH >= a_wl) {
-        // no term of this row here: zeros
-#pragma unroll
-        for (int g = 0; g < kPH / 8; ++g) {
-          const uint32_t off = (uint32_t)((ar >> 3) * kGroupBytes + (ah * (kPH / 8) + g) * 128 + (ar & 7) * 16);
-          *reinterpret_cast<uint4*>(stp + off) = make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4*>(stp + kABytes + off) = make_uint4(0u, 0u, 0u, 0u);
-        }
-      } else {
-#pragma unroll
-        for (int g = 0; g < kPH / 8; ++g) {
-          float v[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float d = dbase - (float)(g * 8 + i);
-            v[i] = ex2(fmaf(-d * d, c, xv[g * 8 + i] * sc) - a_alpha);   // x = -inf -> 0
-          }
-          const int kg = ah * (kPH / 8) + g;              // core-matrix column in the stage
-          const uint32_t off = (uint32_t)((ar >> 3) * kGroupBytes + kg * 128 + (ar & 7) * 16);
-          store_split8(v, stp + off, stp + kABytes + off);
-        }
-      }
-      // B: 8 window positions of output bn per core row
-#pragma unroll
-      for (int q = tid; q < kTN * (kKC / 8); q += kProducerWarps * 32) {
-        const int bn = q % kTN, bq = q / kTN;
-        const float bkap = (float)(bn - kTN / 2);
-        const float bt2 = 2.f * bkap * c, btk = -bkap * bkap * c;
-        // eight consecutive positions: one exponential, then the constant ratio 2^bt2
+  } else if (warp < kProdWarps) {
+    // ---------------------------------------------------------------- producers
+    const int ar = tid & (kTM - 1), aq = tid >> 7;
+    // 128-byte swizzle of the x tile: 16-byte chunk j of row r sits at chunk j ^ (r % 8)
+    const uint32_t xrow = (uint32_t)ar * 128u;
+    const uint32_t xc0 = (uint32_t)(((2 * aq) ^ (ar & 7)) * 16), xc1 = (uint32_t)(((2 * aq + 1) ^ (ar & 7)) * 16);
+    const uint32_t aoff = (uint32_t)((ar >> 3) * kGroupBytes + aq * 128 + (ar & 7) * 16);
+    int xi = 0, oi = 0;
+    bool ok = true;
+    for (int i = 0; i < np && ok; ++i) {
+      const Piece p = piece(i);
+      const BandArgs& a = *p.a;
+      const float c = a.c, sc = a.x_scale;
+      const bool rowok = p.r0 + ar < a.n_rows;
+      float alpha = -INFINITY;
+      for (int ch = p.b; ch < p.e; ++ch) {
+        const int s = xi % kXStages;
+        if (!(ok = mbar_wait(smem_u32(&xfull[s]), (xi / kXStages) & 1, spin, a.err, abort_flag))) break;
+        if (ch == p.b && rowok) alpha = reinterpret_cast<const float*>(xalpha + s * kAlphaBytes)[ar];
+        const float4 x0 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc0);
+        const float4 x1 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc1);
+        mbar_arrive(smem_u32(&xempty[s]));
+        ++xi;
+        const int so = oi % kOpStages;
+        if (oi >= kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / kOpStages) - 1) & 1, spin, a.err, abort_flag))) break;
+        unsigned char* const stp = opring + so * Sh::kOpBytes;
         float v[8];
-        v[0] = ex2(fmaf(bt2, (float)(m0 + bq * 8) - halfW, btk));
-        const float rstep = ex2(bt2);
+        const int m0 = p.lo + ch * kKC + aq * 8;         // absolute position of v[0]
+        if (alpha == -INFINITY) {
 #pragma unroll
-        for (int i = 1; i < 8; ++i) v[i] = __fmul_rn(v[i - 1], rstep);
-        const uint32_t off = (uint32_t)((bn >> 3) * kGroupBytes + bq * 128 + (bn & 7) * 16);
-        store_split8(v, stp + 2 * kABytes + off, stp + 2 * kABytes + kBBytes + off);
+          for (int j = 0; j < 8; ++j) v[j] = 0.f;
+        } else {
+          // exponent e_j = x_j sc - (kc - m0 - j)^2 c - alpha = x_j sc + P + Q j - c j^2
+          const float dbase = (float)(p.kc - m0);
+          const float P = fmaf(-dbase * dbase, c, -alpha), Q = 2.f * dbase * c;
+          const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float K = fmaf(Q, (float)j, fmaf(-(float)(j * j), c, P));
+            v[j] = (m0 + j < a.len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
+          }
+        }
+        store_split8(v, stp + aoff, stp + kABytes + aoff);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&opfull[so]));
+        ++oi;
       }
-      // make the stores visible to the tensor core's async proxy, then arrive
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(&full[s]));
     }
-  }
-  // epilogue geometry: accumulator row = TMEM lane = 32 * (warp % 4) + lane; warps w and w + 4
-  // take the two halves of the TN columns, 8 at a time
-  const int lq = warp & 3, half = (warp >> 2) & 1;
-  const int rloc = 32 * lq + lane;
-  const int r_out = r0 + rloc;
-  // potential update: the marginals of this thread's outputs, loaded while the last MMAs run
-  float lm_pre[kTN / 2];
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q4 = warp & 3;                              // tensor-memory lane quarter
+    const int rl = 32 * q4 + lane;                        // accumulator row
+    const uint32_t tlane = tmem + ((uint32_t)(32 * q4) << 16);
+    const uint32_t tfold = tlane + (uint32_t)(4 * TN);    // running sum of the unit's chunks
+    int ai = 0;
+    bool ok = true;
+    for (int i = 0; i < np && ok; ++i) {
+      const Piece p = piece(i);
+      const BandArgs& a = *p.a;
+      const int row = p.r0 + rl;
+      const bool rowok = row < a.n_rows;
+      const int k1 = min(p.k0 + TN, a.len) - 1;
+      // the potential-update pass: log a of this row's outputs, into shared memory (each thread
+      // loads its own row; across the warp the loads of one output are contiguous)
+      if (MODE == 1 && rowok) {
+        for (int n = 0; n < TN; ++n) {
+          const int k = min(p.k0 + n, k1);
+          const uint32_t dst = smem_u32(s_lm + n * kTM + rl);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(a.lmarg + (size_t)k * a.n_rows + row) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
+      const int ea = i % kEpiAlpha;
+      ok = mbar_wait(smem_u32(&eafull[ea]), (i / kEpiAlpha) & 1, spin, a.err, abort_flag);
+      float alpha = -INFINITY;
+      if (ok) {
+        if (rowok) alpha = reinterpret_cast<const float*>(ealpha + ea * kAlphaBytes)[rl];
+        mbar_arrive(smem_u32(&eaempty[ea]));
+      }
+      if (!epi_all(ok)) break;                            // the same for all 128 threads
+      if (rl == 0) atomicAdd(a.tc_terms, (unsigned long long)(p.e - p.b) * kKC * TN * kTM);
+      const float c = a.c;
+      const float mref = (float)p.lo + 0.5f * (float)(p.S * kKC);
+      bool lm_ready = false;
+      // outputs (o = k0 + c0 + u, r = row) from 16 sums
+      auto emit = [&](int c0, const float* cv16) {
+        if (!rowok) return;
+        if (MODE == 1 && !lm_ready) {
+          asm volatile("cp.async.wait_all;" ::: "memory");
+          lm_ready = true;
+        }
 #pragma unroll
-  for (int u = 0; u < kTN / 2; ++u) {
-    const int k = k0 + half * (kTN / 2) + u;
-    lm_pre[u] = (MODE == 1 && producer && r_out < a.n_rows && k <= k1)
-                    ? a.lmarg[(size_t)k * a.n_rows + r_out] : 0.f;
-  }
-  if (producer) ok = ok && mbar_wait(smem_u32(&done), 0, a.err);
-  ok = __syncthreads_and(ok);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (ok && producer) {
-    const float al = a_alpha;                       // rloc == ar: this thread's own row
-    const float mref = (float)a_lo + halfW;
-#pragma unroll
-    for (int cg = 0; cg < kTN / 2; cg += 8) {
-      const int n0 = half * (kTN / 2) + cg;
-      uint32_t acc[8];
-      const uint32_t taddr = tmem_d + ((uint32_t)(32 * lq) << 16) + (uint32_t)n0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-          : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]),
-            "=r"(acc[6]), "=r"(acc[7])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (r_out < a.n_rows) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int n = n0 + u;
-          const int k = k0 + n;
+        for (int u = 0; u < 16; ++u) {
+          const int n = c0 + u;
+          const int k = p.k0 + n;
           if (k > k1) break;
-          const float kap = (float)(n - kTN / 2);
-          const float cv = __uint_as_float(acc[u]);
+          const float kap = (float)(n - TN / 2);
+          const float cv = cv16[u];
           float out = -INFINITY;
-          if (al != -INFINITY) {
+          if (alpha != -INFINITY) {
             if (cv > 0.f && isfinite(cv))
-              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)kc), c, al), lg2(cv));
+              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)p.kc), c, alpha), lg2(cv));
             else
               raise_error(a.err, FOT_ENONFINITE);
           }
-          const size_t yi = (size_t)k * a.n_rows + r_out;
+          const size_t yi = (size_t)k * a.n_rows + row;
           if (MODE == 0) {
             a.y[yi] = out;
           } else {
             const float sv = __fmul_rn(out, kLn2);
-            const float lm = lm_pre[cg + u];
+            const float lm = s_lm[n * kTM + rl];
             float pot;
             if (lm == -INFINITY) {
               pot = -INFINITY;
@@ -421,19 +645,244 @@ __global__ void __launch_bounds__(kThreadsTC, 2) tc_pass_kernel(const __grid_con
             if (a.logsum) a.logsum[yi] = sv;
           }
         }
+      };
+      for (int j = p.jlo; j < p.jhi; ++j) {
+        const int ab = ai % kAccBufs;
+        ok = mbar_wait(smem_u32(&accfull[ab]), (ai / kAccBufs) & 1, spin, a.err, abort_flag);
+        if (!epi_all(ok)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = tlane + (uint32_t)(ab * 2 * TN);
+        const bool last = j == p.nc - 1;
+        // chunk sum = D[0:TN) + D[TN:2TN) (the three split products), 16 columns at a time; a
+        // split unit's chunk sums go to its slots, the others are added to the running sum
+        float* slot = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN;
+#pragma unroll
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+          uint32_t d1[16], d2[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(d1[0]), "=r"(d1[1]), "=r"(d1[2]), "=r"(d1[3]), "=r"(d1[4]), "=r"(d1[5]), "=r"(d1[6]), "=r"(d1[7]),
+                "=r"(d1[8]), "=r"(d1[9]), "=r"(d1[10]), "=r"(d1[11]), "=r"(d1[12]), "=r"(d1[13]), "=r"(d1[14]), "=r"(d1[15])
+              : "r"(tacc + (uint32_t)c0));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(d2[0]), "=r"(d2[1]), "=r"(d2[2]), "=r"(d2[3]), "=r"(d2[4]), "=r"(d2[5]), "=r"(d2[6]), "=r"(d2[7]),
+                "=r"(d2[8]), "=r"(d2[9]), "=r"(d2[10]), "=r"(d2[11]), "=r"(d2[12]), "=r"(d2[13]), "=r"(d2[14]), "=r"(d2[15])
+              : "r"(tacc + (uint32_t)(TN + c0)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          float cv[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) cv[u] = __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
+          if (p.split) {
+#pragma unroll
+            for (int u = 0; u < 16; u += 4)
+              *reinterpret_cast<float4*>(slot + c0 + u) = make_float4(cv[u], cv[u + 1], cv[u + 2], cv[u + 3]);
+          } else {
+            if (j > 0) {                                  // running sum of chunks 0 .. j-1
+              uint32_t f[16];
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                  : "=r"(f[0]), "=r"(f[1]), "=r"(f[2]), "=r"(f[3]), "=r"(f[4]), "=r"(f[5]), "=r"(f[6]), "=r"(f[7]),
+                    "=r"(f[8]), "=r"(f[9]), "=r"(f[10]), "=r"(f[11]), "=r"(f[12]), "=r"(f[13]), "=r"(f[14]), "=r"(f[15])
+                  : "r"(tfold + (uint32_t)c0));
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+              for (int u = 0; u < 16; ++u) cv[u] = __uint_as_float(f[u]) + cv[u];
+            }
+            if (last) {
+              emit(c0, cv);
+            } else {
+              asm volatile(
+                  "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                  :: "r"(tfold + (uint32_t)c0),
+                     "r"(__float_as_uint(cv[0])), "r"(__float_as_uint(cv[1])), "r"(__float_as_uint(cv[2])), "r"(__float_as_uint(cv[3])),
+                     "r"(__float_as_uint(cv[4])), "r"(__float_as_uint(cv[5])), "r"(__float_as_uint(cv[6])), "r"(__float_as_uint(cv[7])),
+                     "r"(__float_as_uint(cv[8])), "r"(__float_as_uint(cv[9])), "r"(__float_as_uint(cv[10])), "r"(__float_as_uint(cv[11])),
+                     "r"(__float_as_uint(cv[12])), "r"(__float_as_uint(cv[13])), "r"(__float_as_uint(cv[14])), "r"(__float_as_uint(cv[15]))
+                  : "memory");
+            }
+          }
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&accempty[ab]));
+        ++ai;
+      }
+      if (!ok) break;
+      if (p.split) {
+        // the last contributor adds all chunk sums of the unit in chunk order (the same sums,
+        // in the same order, as an unsplit unit) and writes the outputs
+        __threadfence();
+        asm volatile("bar.sync 1, %0;" :: "r"(kEpi) : "memory");
+        if (rl == 0) {
+          // contributors: the distinct CTAs holding a chunk start of the unit (a share shorter
+          // than a chunk can hold none)
+          int ncon = 0, prev = -1;
+          for (int j = 0; j < p.nc; ++j) {
+            const int k = cta_of((long long)p.P + (long long)j * kChunk, S_tot, C);
+            if (k != prev) {
+              ++ncon;
+              prev = k;
+            }
+          }
+          s_last = atomicAdd(&a.ucnt[p.lu], 1) == ncon - 1;
+        }
+        asm volatile("bar.sync 1, %0;" :: "r"(kEpi) : "memory");
+        if (s_last) {
+          __threadfence();
+#pragma unroll
+          for (int c0 = 0; c0 < TN; c0 += 16) {
+            float cv[16];
+            for (int j = 0; j < p.nc; ++j) {
+              const float* sl = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN + c0;
+#pragma unroll
+              for (int u = 0; u < 16; u += 4) {
+                const float4 t4 = __ldcg(reinterpret_cast<const float4*>(sl + u));
+                if (j == 0) {
+                  cv[u] = t4.x;
+                  cv[u + 1] = t4.y;
+                  cv[u + 2] = t4.z;
+                  cv[u + 3] = t4.w;
+                } else {
+                  cv[u] += t4.x;
+                  cv[u + 1] += t4.y;
+                  cv[u + 2] += t4.z;
+                  cv[u + 3] += t4.w;
+                }
+              }
+            }
+            emit(c0, cv);
+          }
+          if (rl == 0) a.ucnt[p.lu] = 0;
+        }
       }
     }
   }
+
+  // ---- units outside the tensor path: CUDA-core window sums by the producer warps ------------
+  // (every x tile has been consumed, so the x ring is free as scratch)
+  if (warp < kProdWarps && !*abort_flag) {
+    float* sAw = reinterpret_cast<float*>(xring) + warp * 2 * kSA;
+    for (int d = 0; d < nd; ++d) {
+      const int u = s_decl[d];
+      const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, u)];
+      const int lu = u - a.cta_base;
+      const int tile = lu % a.n_tiles;
+      tc_cuda_core_unit<MODE, TN>(a, (lu / a.n_tiles) * kTM, tile, tile * TN, warp, sAw);
+    }
+  }
+
+  // ---- tear-down --------------------------------------------------------------------------
+  __syncthreads();
+  if (*abort_flag) {
+    // wait (bounded, with the full limit) for the copies and MMAs this CTA started
+    if (warp == kTmaWarp && lane == 0) {
+      for (int s = 0; s < kXStages && s < issued_x; ++s)
+        mbar_drain(smem_u32(&xfull[s]), ((issued_x - 1 - s) / kXStages) & 1);
+      for (int s = 0; s < kOpStages && s < issued_o; ++s)
+        mbar_drain(smem_u32(&bfull[s]), ((issued_o - 1 - s) / kOpStages) & 1);
+      for (int s = 0; s < kEpiAlpha && s < issued_ea; ++s)
+        mbar_drain(smem_u32(&eafull[s]), ((issued_ea - 1 - s) / kEpiAlpha) & 1);
+    }
+    if (warp == kMmaWarp && lane == 0 && issued_mma) {
+      mma_commit(smem_u32(&drain));
+      mbar_drain(smem_u32(&drain), 0);
+    }
+    if (tid < kEpi + kEpiWarp0 * 32 && tid >= kEpiWarp0 * 32 && MODE == 1)
+      asm volatile("cp.async.wait_all;" ::: "memory");
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == kProducerWarps)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_d), "r"(kTmemCols)
-                 : "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == kMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Sh::kTmemCols) : "memory");
+}
+
+// B operand table of one pass: for every half-shift s = e - s_max (e in [0, 2 s_max)) the
+// block of 2 TN rows x 32 positions in the canonical K-major core-matrix layout, rows n < TN
+// B_hi and rows TN + n B_lo of B(u, kap) = 2^(2 kap (16 s + u) c - kap^2 c), kap = n - TN/2
+// (a stage at window offset 32 ch in a window of nW stages reads block e = 2 ch - nW + s_max:
+// m' - W/2 = 16 (2 ch - nW) + u).  Exponents are clamped to [-126, 126]: blocks whose values
+// would leave that range only serve units outside the tilt bound, which never read them.
+template <int TN>
+__global__ void btab_kernel(unsigned char* tab, int s_max, float c) {
+  constexpr int kBBytes = 2 * TN * kKC * 2;
+  const int gi = blockIdx.x * blockDim.x + threadIdx.x;   // (e, n, kg)
+  const int kg = gi & 3, n = (gi >> 2) % TN, e = (gi >> 2) / TN;
+  if (e >= 2 * s_max) return;
+  const float kap = (float)(n - TN / 2);
+  const float sh = 16.f * (float)(e - s_max) + (float)(8 * kg);
+  float v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const float ex = fmaf(2.f * kap * (sh + (float)u), c, -kap * kap * c);
+    v[u] = ex2(fminf(fmaxf(ex, -126.f), 126.f));
+  }
+  unsigned char* blk = tab + (size_t)e * kBBytes;
+  const int rh = n, rl = TN + n;
+  store_split8(v, blk + (rh >> 3) * kGroupBytes + kg * 128 + (rh & 7) * 16,
+               blk + (rl >> 3) * kGroupBytes + kg * 128 + (rl & 7) * 16);
+}
+
+// ---- host side ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// the x tensor map of a pass: [n_rows][len] FP32, boxes of 32 positions x 128 rows, 128-byte
+// swizzle; positions and rows outside the image read as zeros (the kernel masks them)
+bool encode_xmap(BandArgs& a) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if ((a.len & 3) != 0 || (reinterpret_cast<uintptr_t>(a.x) & 15u) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)a.len, (cuuint64_t)a.n_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)a.len * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)kTM};
+  cuuint32_t estr[2] = {1, 1};
+  static_assert(sizeof(CUtensorMap) == sizeof(a.xmap), "tensor map size");
+  return fn(reinterpret_cast<CUtensorMap*>(a.xmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 struct TcState {
-  unsigned long long* tc_terms = nullptr; // window terms computed on the tensor cores
+  unsigned long long* tc_terms = nullptr;   // window terms computed on the tensor cores
+  int* ext = nullptr;          // [2 parities][lo, hi][max units]
+  int* ucnt = nullptr;         // [max units]
+  unsigned char* btab = nullptr;
+  float* slots = nullptr;      // chunk sums of split units: [sms][slot_chunks][128][64]
+  int max_units = 0, s_max = 0, slot_chunks = 0, sms = 0, parity = 0, spin = kSpinDefault;
+  float btab_c = 0.f;          // parameters of the B table as last written on the stream
+  int btab_tn = 0;
 };
+
+size_t btab_bytes(int s_max) { return (size_t)2 * s_max * TcShape<64>::kBBytes; }
+
+template <int TN, int MAXP>
+void set_smem_attr(bool& ok) {
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, TN, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TcShape<TN>::kSmemBytes) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, TN, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TcShape<TN>::kSmemBytes) == cudaSuccess;
+}
 
 }  // namespace
 
@@ -442,39 +891,49 @@ bool tc_supported(int rows, int cols) { return rows >= 1 && cols >= 1; }
 int tc_create(fot_ctx* c) {
   TcState* t = new (std::nothrow) TcState();
   if (!t) return 1;
-  if (cudaMalloc((void**)&t->tc_terms, sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemsetAsync(t->tc_terms, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
-    if (t->tc_terms) cudaFree(t->tc_terms);
-    delete t;
-    return 1;
+  const int rows = c->rows, cols = c->cols;
+  t->max_units = std::max(((rows + 127) / 128) * ((cols + 15) / 16), ((cols + 127) / 128) * ((rows + 15) / 16));
+  t->s_max = (std::max(rows, cols) + kKC - 1) / kKC;
+  t->slot_chunks = (t->s_max + kChunk - 1) / kChunk;
+  if (cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || t->sms < 1) t->sms = 1;
+  if (const char* e = getenv("FOT_TEST_WAIT_LIMIT")) {   // test-only: a short wait limit
+    const int v = atoi(e);
+    if (v > 0) t->spin = v;
   }
-  // dynamic shared memory above 48 KB, for every instance (before any stream capture)
-  bool ok = true;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 16, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<16>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 32, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 32, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<32>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 64, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<0, 64, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(tc_pass_kernel<1, 64, kMaxBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcShape<64>::kSmemBytes) == cudaSuccess;
-  if (!ok) {
-    cudaFree(t->tc_terms);
-    delete t;
-    return 1;
+  bool ok = cudaMalloc((void**)&t->tc_terms, sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&t->ext, (size_t)4 * t->max_units * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&t->ucnt, (size_t)t->max_units * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&t->btab, btab_bytes(t->s_max)) == cudaSuccess;
+  ok = ok && cudaMalloc((void**)&t->slots, (size_t)t->sms * t->slot_chunks * kTM * 64 * sizeof(float)) == cudaSuccess;
+  if (ok) {
+    // reset state of the unit extents (lo = 0x7F7F7F7F, hi = 0) and the split counters
+    for (int p = 0; p < 2; ++p) {
+      ok = ok && cudaMemsetAsync(t->ext + (size_t)(2 * p) * t->max_units, 0x7F, (size_t)t->max_units * sizeof(int), c->stream) == cudaSuccess;
+      ok = ok && cudaMemsetAsync(t->ext + (size_t)(2 * p + 1) * t->max_units, 0, (size_t)t->max_units * sizeof(int), c->stream) == cudaSuccess;
+    }
+    ok = ok && cudaMemsetAsync(t->ucnt, 0, (size_t)t->max_units * sizeof(int), c->stream) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(t->tc_terms, 0, sizeof(unsigned long long), c->stream) == cudaSuccess;
   }
+  // dynamic shared memory above 48 KB, for every instance (per device; before any capture)
+  set_smem_attr<16, 1>(ok);
+  set_smem_attr<32, 1>(ok);
+  set_smem_attr<64, 1>(ok);
+  set_smem_attr<16, kMaxBatch>(ok);
+  set_smem_attr<32, kMaxBatch>(ok);
+  set_smem_attr<64, kMaxBatch>(ok);
   c->tc = t;
+  if (!ok) return 1;   // fot_create destroys the context (tc_destroy frees what was made)
   return 0;
 }
 
 void tc_destroy(fot_ctx* c) {
   TcState* t = (TcState*)c->tc;
   if (!t) return;
-  cudaFree(t->tc_terms);
+  if (t->tc_terms) cudaFree(t->tc_terms);
+  if (t->ext) cudaFree(t->ext);
+  if (t->ucnt) cudaFree(t->ucnt);
+  if (t->btab) cudaFree(t->btab);
+  if (t->slots) cudaFree(t->slots);
   delete t;
   c->tc = nullptr;
 }
@@ -488,13 +947,57 @@ int64_t tc_terms(fot_ctx* c) {
   return (int64_t)v;
 }
 
+unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
+
+// Start of a sequence of passes of one API call (a solve, a graph capture, a standalone
+// half-step): the B table is rewritten at its first tensor pass, and the split counters start
+// from zero (a pass that timed out can leave them set).
+void tc_begin(fot_ctx* c) {
+  TcState* t = (TcState*)c->tc;
+  if (!t) return;
+  t->btab_tn = 0;
+  cudaMemsetAsync(t->ucnt, 0, (size_t)t->max_units * sizeof(int), c->stream);
+}
+
+// The tensor-core fields of one pass's arguments: unit extents of the current parity (and the
+// other parity, which this pass's plan kernel resets), split counters, B table.  Toggles the
+// parity: call once per pass.
+void tc_bind(fot_ctx* c, BandArgs& a) {
+  TcState* t = (TcState*)c->tc;
+  const int p = t->parity;
+  t->parity ^= 1;
+  a.ext_lo = t->ext + (size_t)(2 * p) * t->max_units;
+  a.ext_hi = t->ext + (size_t)(2 * p + 1) * t->max_units;
+  a.ext_lo_next = t->ext + (size_t)(2 * (p ^ 1)) * t->max_units;
+  a.ext_hi_next = t->ext + (size_t)(2 * (p ^ 1) + 1) * t->max_units;
+  a.ext_units = t->max_units;
+  a.ucnt = t->ucnt;
+  a.btab = t->btab;
+  a.s_max = t->s_max;
+  a.tc_terms = t->tc_terms;
+}
+
+// whether the B table of ctx c needs writing for (kernel constant cc, tile width tw); records
+// the new parameters
+bool tc_btab_stale(fot_ctx* c, float cc, int tw) {
+  TcState* t = (TcState*)c->tc;
+  if (t->btab_tn == tw && t->btab_c == cc) return false;
+  t->btab_tn = tw;
+  t->btab_c = cc;
+  return true;
+}
+
+float* tc_slots(fot_ctx* c) { return ((TcState*)c->tc)->slots; }
+int tc_sms(fot_ctx* c) { return ((TcState*)c->tc)->sms; }
+int tc_spin(fot_ctx* c) { return ((TcState*)c->tc)->spin; }
+
 // Tile width of a tensor-core pass for a problem with kernel constant c: the widest TN in
 // {64, 32} whose tile is expected to meet the tilt bound |kap| W c <= kTiltMaxTC with room to
 // spare: W is taken as twice the window of a smooth potential (the tile plus sqrt(kCut / c) on
 // each side, where the Gaussian kernel alone has fallen by 2^-kCut), rounded up to a multiple
 // of 64 positions, since the hull of a tile's windows grows where the transport map jumps across
 // zero-mass gaps; else 16 when a 16-wide tile meets the bound with a window of kRouteKC
-// positions; else 0: the CUDA-core kernel.  A declined wide tile costs exact window sums.
+// positions; else 0: the CUDA-core kernel.  A unit outside the bound costs CUDA-core window sums.
 int tc_width_for(float c) {
   for (int tn = 64; tn >= 32; tn /= 2) {
     const float w = (float)tn + 2.f * sqrtf(kCut / c);
@@ -505,52 +1008,113 @@ int tc_width_for(float c) {
   return 0;
 }
 
-// tw: the tile width every problem of the table uses (tc_width_for of its c)
-template <int MODE, int MAXP>
-int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw) {
-  for (int q = 0; q < t.n; ++q) t.p[q].tile_w = tw == 0 ? kBT : tw;
-  band_table_finish(t);
-  band_prepare(s, t);
-  if (tw == 0) {
-    band_simt<MODE>(s, t);
-    return 2;
-  }
-  ktimer_begin(s, kKTensor);
-  if (tw == 64)
-    tc_pass_kernel<MODE, 64, MAXP><<<t.ctas, kThreadsTC, TcShape<64>::kSmemBytes, s>>>(t);
-  else if (tw == 32)
-    tc_pass_kernel<MODE, 32, MAXP><<<t.ctas, kThreadsTC, TcShape<32>::kSmemBytes, s>>>(t);
-  else
-    tc_pass_kernel<MODE, 16, MAXP><<<t.ctas, kThreadsTC, TcShape<16>::kSmemBytes, s>>>(t);
+template <int TN, int MAXP>
+static void launch_btab(cudaStream_t s, const BandArgs& a) {
+  const int threads = 2 * a.s_max * TN * 4;
+  ktimer_begin(s, kKPlan);                 // timed with the window plans (set-up of a pass)
+  btab_kernel<TN><<<(threads + 255) / 256, 256, 0, s>>>(const_cast<unsigned char*>(a.btab), a.s_max, a.c);
   ktimer_end(s);
-  return 2;
 }
 
-unsigned long long* tc_terms_ptr(fot_ctx* c) { return c->tc ? ((TcState*)c->tc)->tc_terms : nullptr; }
-template int tc_pass<0, 1>(cudaStream_t, BandTable<1>&, int);
-template int tc_pass<1, 1>(cudaStream_t, BandTable<1>&, int);
-template int tc_pass<0, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int);
-template int tc_pass<1, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int);
+// tw: the tile width every problem of the table uses (tc_width_for of its c); ctx[q]: the
+// context of problem q (its B table is rewritten first when stale); ctx[0] also lends the
+// split slots, the SM count and the wait limit.  Returns the number of kernels launched.
+template <int MODE, int MAXP>
+int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx) {
+  // the problems the tensor kernel can take (rows 16-byte aligned for the tensor copies) and
+  // the others, each in a table of its own
+  BandTable<MAXP>* tt = new BandTable<MAXP>();
+  BandTable<MAXP>* tf = new BandTable<MAXP>();
+  fot_ctx* tctx[MAXP];
+  for (int q = 0; q < t.n; ++q) {
+    BandArgs a = t.p[q];
+    a.tile_w = tw == 0 ? kBT : tw;
+    if (tw != 0 && encode_xmap(a)) {
+      tctx[tt->n] = ctx[q];
+      tt->p[tt->n++] = a;
+    } else {
+      a.ext_lo = a.ext_hi = nullptr;   // the plan kernel still resets the next pass's extents
+      a.tile_w = kBT;
+      tf->p[tf->n++] = a;
+    }
+  }
+  int k = 0;
+  if (tt->n > 0) {
+    band_table_finish(*tt);
+    // the context with the most slot chunks lends its slots (every problem's chunks fit)
+    TcState* ts = (TcState*)tctx[0]->tc;
+    for (int q = 1; q < tt->n; ++q) {
+      TcState* o = (TcState*)tctx[q]->tc;
+      if (o->slot_chunks > ts->slot_chunks) ts = o;
+    }
+    const int sms = ts->sms;
+    if (tt->ctas > kThreads * kUnitsPerThread || tt->ctas > (kMaxPieces / 2) * sms) {
+      // more units than the kernel's set-up holds: the CUDA-core sums for all of them
+      for (int q = 0; q < tt->n; ++q) {
+        BandArgs a = tt->p[q];
+        a.ext_lo = a.ext_hi = nullptr;
+        a.tile_w = kBT;
+        tf->p[tf->n++] = a;
+      }
+      tt->n = 0;
+    } else {
+      for (int q = 0; q < tt->n; ++q) {
+        if (!tc_btab_stale(tctx[q], tt->p[q].c, tw)) continue;
+        if (tw == 64) launch_btab<64, MAXP>(s, tt->p[q]);
+        else if (tw == 32) launch_btab<32, MAXP>(s, tt->p[q]);
+        else launch_btab<16, MAXP>(s, tt->p[q]);
+        ++k;
+      }
+      band_prepare(s, *tt);
+      tt->slots = ts->slots;
+      tt->slot_chunks = ts->slot_chunks;
+      tt->spin_limit = ts->spin;
+      const int grid = std::max(1, std::min(sms, tt->ctas));
+      ktimer_begin(s, kKTensor);
+      if (tw == 64)
+        tc_pass_kernel<MODE, 64, MAXP><<<grid, kThreads, TcShape<64>::kSmemBytes, s>>>(*tt);
+      else if (tw == 32)
+        tc_pass_kernel<MODE, 32, MAXP><<<grid, kThreads, TcShape<32>::kSmemBytes, s>>>(*tt);
+      else
+        tc_pass_kernel<MODE, 16, MAXP><<<grid, kThreads, TcShape<16>::kSmemBytes, s>>>(*tt);
+      ktimer_end(s);
+      k += 2;
+    }
+  }
+  if (tf->n > 0) {
+    band_table_finish(*tf);
+    band_prepare(s, *tf);
+    band_simt<MODE>(s, *tf);
+    k += 2;
+  }
+  delete tt;
+  delete tf;
+  return k;
+}
+
+template int tc_pass<0, 1>(cudaStream_t, BandTable<1>&, int, fot_ctx* const*);
+template int tc_pass<1, 1>(cudaStream_t, BandTable<1>&, int, fot_ctx* const*);
+template int tc_pass<0, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int, fot_ctx* const*);
+template int tc_pass<1, kMaxBatch>(cudaStream_t, BandTable<kMaxBatch>&, int, fot_ctx* const*);
 
 BandArgs band_args(fot_ctx* c, const float* x, int n_rows, int len, double eps, float x_scale);
 
 // One half-step with the tensor-core banded passes.
 void half_step_tc(fot_ctx* c, const float* pot_in, const float* lmarg, double eps, float* pot_out,
                   float* logsum) {
-  TcState* ts = (TcState*)c->tc;
   BandTable<1> t{};
   t.n = 1;
   t.p[0] = band_args(c, pot_in, c->rows, c->cols, eps, (float)(1.4426950408889634 / eps));
   t.p[0].y = c->R;
-  t.p[0].tc_terms = ts->tc_terms;
+  tc_bind(c, t.p[0]);
   const int tw = tc_width_for(t.p[0].c);
-  int k = tc_pass<0>(c->stream, t, tw);
+  int k = tc_pass<0>(c->stream, t, tw, &c);
   t.p[0] = band_args(c, c->R, c->cols, c->rows, eps, 1.f);
   t.p[0].y = pot_out;
   t.p[0].lmarg = lmarg;
   t.p[0].logsum = logsum;
-  t.p[0].tc_terms = ts->tc_terms;
-  k += tc_pass<1>(c->stream, t, tw);
+  tc_bind(c, t.p[0]);
+  k += tc_pass<1>(c->stream, t, tw, &c);
   c->launches += k;
 }
 

@@ -53,3 +53,28 @@ def test_noalloc_rejects_oversize(fot_lib):
         B._check(B._lib.fot_u_update_noalloc(B._ptr(big), B._ptr(big), 1025, 1024, 1.0,
                                              B._ptr(big), None, B._stream()), "noalloc")
     assert e.value.status == 1                      # FOT_EINVAL, nothing launched
+
+
+def test_noalloc_allocates_nothing(fot_lib):
+    """The entry point's contract: after a first call (the one-time set-up and the lazy
+    loading of its kernels), further calls change neither the device's free memory nor
+    torch's allocator state."""
+    B = fot_lib
+    shape, eps = (1024, 1024), 209.7
+    rng = np.random.default_rng(23)
+    g = f32(rng.uniform(0.05, 1.0, size=shape))
+    la = _log_marginal(g)
+    psi = to_dev(f32(inputs.random_potential(*shape, scale=0.3 * 1024 * 1024, seed=41, zero_frac=0.1)))
+    f = torch.empty(shape, device="cuda")
+    S = torch.empty(shape, device="cuda")
+    B.fot_u_update_noalloc(psi, la, eps, f_out=f, logsum_out=S)     # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        B.fot_u_update_noalloc(psi, la, eps, f_out=f, logsum_out=S)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0, (free0, free1)
+    assert torch.isfinite(f[torch.isfinite(la)]).all()
