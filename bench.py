@@ -212,10 +212,7 @@ N_SM = 152
 # capture of the current build on the benchmark workload (the capture and its command are in the
 # named profiles/ summary).  Keyed by (kernel, n, precision); a kernel that changes since its
 # capture must lose its entry (the bench line then reports traffic null).
-NCU_TRAFFIC = {
-    ("tc_pass_kernel", 1024, "mixed"): {"bytes": 3159296, "source": "profiles/tc_pass_kernel_c3_1024_mixed.md (row-pass launch)"},
-    ("band_pass_kernel", 1024, "fp32"): {"bytes": 3770112, "source": "profiles/band_pass_kernel_c3_1024_fp32.md (row-pass launch)"},
-}
+NCU_TRAFFIC = {}
 
 
 def _roofline(n, a, ktimes, work, loop_ms):
@@ -249,10 +246,20 @@ def _roofline(n, a, ktimes, work, loop_ms):
                 "peak_source": f"MUFU ex2 {EX2_PER_CLK_PER_SM}/clk/SM x {N_SM} SMs x {clk_mhz:.0f} MHz",
                 "gemm_window_terms": gemm / steps}
     elif dom == "tc_pass_kernel":
+        # algorithmic work of the dense separable iteration: 8 n^3 flop per iteration (2 n^3 per
+        # axis pass: n rows x n outputs x n terms, one multiply-add each), over the time of the
+        # tensor kernel's own launches; the flops it executed (3 BF16 multiply-adds per window
+        # term of the union windows) are reported beside it
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
-        roof = {"bound": "tensor", "achieved": 6.0 * tensor / sec / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "work": "3 BF16 multiply-adds (split precision) per tensor-core term",
+        algo = 8.0 * n ** 3 * a.iters * steps
+        roof = {"bound": "tensor", "achieved": algo / sec / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "work": "8 n^3 flop per iteration (the dense separable contraction of "
+                                           "Sec. 3: 4 axis passes of n^3 multiply-adds) over the tensor "
+                                           "kernel's event time",
                 "peak_source": "cuBLAS bf16 sustained, " + peak_src,
+                "executed_tflops": 6.0 * tensor / sec / 1e12,
+                "executed_frac": 6.0 * tensor / sec / 1e12 / peak,
+                "executed_work": "3 BF16 multiply-adds (split precision) per window term computed",
                 "cuda_core_terms_in_kernel": (gemm + exact) / steps}
     elif dom == "axis_pass_kernel":
         roof = {"bound": "alu", "achieved": dense / sec / 1e12, "peak": ex2_peak, "unit": "Tex2/s",

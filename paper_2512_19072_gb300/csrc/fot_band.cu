@@ -36,14 +36,16 @@
 namespace fot {
 
 // Per (row, tile) plan (tiles of tile_w = 16, 32 or 64 outputs): offset alpha, window start
-// lo and window length wl.  One warp per row; the row is staged in shared memory as
-// z[m] = x[m] * scale in 32-wide chunks (one pad word per chunk), with each chunk's maximum
-// cm[j] and the position p[j] where it is reached.  Lane t then takes tiles t, t + 32, ...:
+// lo and window length wl.  A CTA takes R whole rows; each row is staged once in shared memory
+// as z[m] = x[m] * scale in 32-wide chunks (one pad word per chunk), with each chunk's maximum
+// cm[j] and the position p[j] where it is reached.  Then four lanes (q = 0..3) work on each
+// tile, eight tiles per warp, splitting the chunks (j = q mod 4) and the positions of a
+// scanned chunk (8 each) between them:
 //   a. alpha: the largest term e(m, kc) = z[m] - (kc - m)^2 c at the tile centre kc over the
 //      positions of the chunks scanned: first the chunk whose own maximum gives the best
 //      term at kc (e(p[j], kc)), then every chunk whose bound cm[j] - d_j^2 c (d_j its
-//      nearest distance to kc) exceeds the best term found so far by more than kPlanSlack.
-//      Every unscanned chunk is then within kPlanSlack of alpha, so
+//      nearest distance to kc) exceeds the best term found so far by more than kPlanSlack,
+//      lowest first.  Every unscanned chunk is then within kPlanSlack of alpha, so
 //          alpha_exact - kPlanSlack <= alpha <= alpha_exact.
 //      An offset below the exact maximum only raises the operands 2^(e - alpha) (by at most
 //      2^kPlanSlack): the range arguments of the GEMM paths only need alpha <= alpha_exact.
@@ -51,59 +53,88 @@ namespace fot {
 //      e(mh, o) for the position mh that gave alpha (valid for every output of the tile, as
 //      e(mh, o) is concave in o): the first and the last chunk whose bound over the tile
 //      reaches LB - kCut.
-constexpr int kPlanWarps = 8;        // rows per CTA (fewer for long rows: see band_prepare)
-constexpr float kPlanSlack = 8.f;    // log2 units
+// With unit extents requested (tensor-core passes) the CTA also reduces, per tile, the union
+// of its rows' windows into the unit's [ext_lo, ext_hi) (all R rows lie in one 128-row block).
+constexpr int kPlanWarps = 8;                 // rows per CTA at most (plan rows are padded to a multiple)
+constexpr int kPlanMaxChunks = 4096 / kCW;    // 32-wide chunks of the longest row
+constexpr int kPlanQ = 4;                     // lanes per tile
+constexpr int kPlanTPW = 32 / kPlanQ;         // tiles per warp
+constexpr float kPlanSlack = 8.f;             // log2 units
 
 // shared memory of one row (floats): z[n_chunks * 33], cm[n_chunks], p[n_chunks] (as float)
 __host__ __device__ inline int plan_row_floats(int n_chunks) { return n_chunks * (kCW + 3); }
 
+// max with the smaller key on ties, over the kPlanQ lanes of a tile
+__device__ __forceinline__ void quad_argmax(float& v, int& k) {
+#pragma unroll
+  for (int d = 1; d < kPlanQ; d <<= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, d);
+    const int ok = __shfl_xor_sync(0xffffffffu, k, d);
+    if (ov > v || (ov == v && ok < k)) {
+      v = ov;
+      k = ok;
+    }
+  }
+}
+
 template <int MAXP>
-__global__ void __launch_bounds__(kPlanWarps * 32) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
+__global__ void __launch_bounds__(1024) band_plan_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   extern __shared__ __align__(16) float s_plan[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  // every warp of a CTA belongs to one problem and one 128-row block: each problem's plan rows
-  // start at a multiple of 8 and nwarps divides 8
-  const int grow = blockIdx.x * nwarps + warp;
-  const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, (int)blockIdx.x * nwarps)];
-  const int row = grow - a.plan_base;                       // may be a padding row (>= n_rows)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wpr = tab.plan_wpr;                           // warps per row
+  const int R = (blockDim.x >> 5) / wpr;                  // rows of this CTA
+  const int rr = warp / wpr, wr = warp % wpr;             // this warp's row and tile group
+  // every row of a CTA belongs to one problem and one 128-row block: each problem's plan rows
+  // start at a multiple of 8 and R divides 8
+  const int grow0 = (int)blockIdx.x * R;
+  const BandArgs& a = tab.p[find_prob<MAXP, 1>(tab, grow0)];
+  const int row = grow0 + rr - a.plan_base;               // may be a padding row (>= n_rows)
   const int T = a.n_tiles, len = a.len, nch = a.n_chunks, tw = a.tile_w;
   const bool live = row < a.n_rows && !error_latched(a.err);
   const bool ext = a.ext_lo != nullptr;
-  int* s_ulo = reinterpret_cast<int*>(s_plan + (size_t)nwarps * tab.plan_row_stride);
+  float* z = s_plan + (size_t)rr * tab.plan_row_stride;
+  float* cm = z + nch * (kCW + 1);
+  float* cp = cm + nch;
+  int* s_ulo = reinterpret_cast<int*>(s_plan + (size_t)R * tab.plan_row_stride);
   int* s_uhi = s_ulo + tab.plan_tiles;
   if (a.ext_lo_next) {
     // reset the next pass's unit extents (the problem's plan rows take strided shares; the
     // next pass's plan kernel reduces into them): the whole array, since the next pass may
     // contract the other axis with another tile width
-    for (int i = row * 32 + lane; i < a.ext_units; i += a.plan_rows * 32) {
-      a.ext_lo_next[i] = 0x7F7F7F7F;
-      a.ext_hi_next[i] = 0;
-    }
+    if (wr == 0)
+      for (int i = row * 32 + lane; i < a.ext_units; i += a.plan_rows * 32) {
+        a.ext_lo_next[i] = 0x7F7F7F7F;
+        a.ext_hi_next[i] = 0;
+      }
   }
-  if (ext) {
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+  if (ext)
+    for (int t = tid; t < T; t += blockDim.x) {
       s_ulo[t] = 0x7F7F7F7F;
       s_uhi[t] = 0;
     }
-    __syncthreads();                                       // CTA-uniform (ext is per problem)
-  }
+  const float c = a.c, sc = a.x_scale;
+  // stage the rows (each warp of a row loads every wpr-th chunk, coalesced, eight in flight)
   if (live) {
-    const float c = a.c, sc = a.x_scale;
     const float* xr = a.x + (size_t)row * len;
-    float* z = s_plan + (size_t)warp * tab.plan_row_stride;
-    float* cm = z + nch * (kCW + 1);
-    float* cp = cm + nch;
-
-    // stage the row (coalesced: one 128-byte chunk per warp load)
-#pragma unroll 4
-    for (int j = 0; j < nch; ++j) {
-      const int m = j * kCW + lane;
-      z[j * (kCW + 1) + lane] = m < len ? __fmul_rn(xr[m], sc) : -INFINITY;
+    for (int j0 = wr; j0 < nch; j0 += 8 * wpr) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + q * wpr, m = j * kCW + lane;
+        v[q] = (j < nch && m < len) ? __fmul_rn(__ldg(xr + m), sc) : -INFINITY;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = j0 + q * wpr;
+        if (j < nch) z[j * (kCW + 1) + lane] = v[q];
+      }
     }
-    __syncwarp();
-    // chunk maxima and their leftmost positions: lane j takes chunks j, j + 32, ... (the pad
-    // word puts the 32 lanes on 32 different banks)
-    for (int j = lane; j < nch; j += 32) {
+  }
+  __syncthreads();
+  // chunk maxima and their leftmost positions (thread per chunk; the pad word puts the lanes
+  // of a warp on different banks)
+  if (live) {
+    for (int j = wr * 32 + lane; j < nch; j += wpr * 32) {
       const float* zj = z + j * (kCW + 1);
       float best = -INFINITY;
       int arg = 0;
@@ -118,19 +149,31 @@ __global__ void __launch_bounds__(kPlanWarps * 32) band_plan_kernel(const __grid
       cm[j] = best;
       cp[j] = (float)(j * kCW + arg);
     }
-    __syncwarp();
+  }
+  __syncthreads();
 
+  if (live) {
     const size_t np = (size_t)a.plan_stride * T;
     float* p_alpha = a.plan;
     int* p_lo = reinterpret_cast<int*>(a.plan + np);
     int* p_wl = reinterpret_cast<int*>(a.plan + 2 * np);
-    for (int t = lane; t < T; t += 32) {
-      const int k0 = t * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
+    const int q = lane & (kPlanQ - 1);
+    // warp-uniform loop over this warp's groups of eight tiles (the combines and the candidate
+    // rounds below are warp-wide); lanes of a missing tile compute nothing and write nothing
+    for (int tg = wr * kPlanTPW; tg < T; tg += wpr * kPlanTPW) {
+      const int t = tg + lane / kPlanQ;
+      const bool has = t < T;
+      const int k0 = min(t, T - 1) * tw, kc = k0 + tw / 2, k1 = min(k0 + tw, len) - 1;
       const float fkc = (float)kc;
+      auto bound = [&](int j) {                           // chunk j's bound at kc
+        const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
+        const int dd = clo > kc ? clo - kc : (chi < kc ? kc - chi : 0);
+        return fmaf(-(float)dd * (float)dd, c, cm[j]);
+      };
       // a. the chunk whose maximum gives the best term at kc
       float vb = -INFINITY;
-      int jb = -1;
-      for (int j = 0; j < nch; ++j) {
+      int jb = 0x7fffffff;
+      for (int j = q; j < nch && has; j += kPlanQ) {
         const float d = fkc - cp[j];
         const float v = fmaf(-d * d, c, cm[j]);
         if (v > vb) {
@@ -138,44 +181,80 @@ __global__ void __launch_bounds__(kPlanWarps * 32) band_plan_kernel(const __grid
           jb = j;
         }
       }
+      quad_argmax(vb, jb);
       float alpha = -INFINITY;
-      int mh = 0;
-      auto scan = [&](int j) {                            // exact maximum over chunk j
-        const float* zj = z + j * (kCW + 1);
-        float d = fkc - (float)(j * kCW);
-#pragma unroll 8
-        for (int u = 0; u < kCW; ++u, d -= 1.f) {
+      int mh = 0x7fffffff;
+      // exact maximum over chunk j, the four lanes taking eight positions each; every lane of
+      // the warp runs it (the combine is warp-wide), a lane whose tile has nothing to scan
+      // passes valid = false and keeps its maximum
+      auto scan = [&](int j, bool valid) {
+        const float* zj = z + j * (kCW + 1) + q * (kCW / kPlanQ);
+        float d = fkc - (float)(j * kCW + q * (kCW / kPlanQ));
+        float v0 = -INFINITY;
+        int m0 = 0x7fffffff;
+#pragma unroll
+        for (int u = 0; u < kCW / kPlanQ; ++u, d -= 1.f) {
           const float v = fmaf(-d * d, c, zj[u]);
-          if (v > alpha) {
-            alpha = v;
-            mh = j * kCW + u;
+          if (v > v0) {
+            v0 = v;
+            m0 = j * kCW + q * (kCW / kPlanQ) + u;
           }
         }
+        quad_argmax(v0, m0);
+        if (valid && (v0 > alpha || (v0 == alpha && m0 < mh))) {
+          alpha = v0;
+          mh = m0;
+        }
       };
-      if (jb >= 0) {
-        scan(jb);
-        for (int j = 0; j < nch; ++j) {
-          if (j == jb) continue;
-          const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
-          const int dd = clo > kc ? clo - kc : (chi < kc ? kc - chi : 0);
-          if (fmaf(-(float)dd * (float)dd, c, cm[j]) > alpha + kPlanSlack) scan(j);
+      const bool any = has && vb != -INFINITY;
+      if (__any_sync(0xffffffffu, any)) {
+        scan(any ? jb : 0, any);
+        // the candidate chunks (this lane's share), then rounds in which every tile scans its
+        // lowest remaining candidate together; each is tested again against the maximum so far
+        uint32_t cand[kPlanMaxChunks / 32 / kPlanQ + 1];
+#pragma unroll
+        for (int w = 0; w < kPlanMaxChunks / 32 / kPlanQ + 1; ++w) cand[w] = 0u;
+        if (any)
+          for (int j = q, b = 0; j < nch; j += kPlanQ, ++b)
+            if (j != jb && bound(j) > alpha + kPlanSlack) cand[b >> 5] |= 1u << (b & 31);
+        for (;;) {
+          int mine = 0x7fffffff;                          // this lane's lowest candidate chunk
+#pragma unroll
+          for (int w = 0; w < kPlanMaxChunks / 32 / kPlanQ + 1; ++w)
+            if (mine == 0x7fffffff && cand[w] != 0u) mine = (w * 32 + __ffs(cand[w]) - 1) * kPlanQ + q;
+          float dummy = 0.f;
+          int next = mine;
+          quad_argmax(dummy, next);                       // the tile's lowest candidate
+          if (!__any_sync(0xffffffffu, next != 0x7fffffff)) break;
+          if (next != 0x7fffffff && next == mine) {
+            const int b = (mine - q) / kPlanQ;
+            cand[b >> 5] &= ~(1u << (b & 31));
+          }
+          const bool doscan = next != 0x7fffffff && bound(next) > alpha + kPlanSlack;
+          scan(doscan ? next : 0, doscan);
         }
       }
       // b. window
-      int wlo = -1, whi = -1;
-      if (alpha != -INFINITY) {
+      int wlo = 0x7fffffff, whi = -1;
+      if (has && alpha != -INFINITY) {
         const float zm = z[(mh / kCW) * (kCW + 1) + mh % kCW];
         const float da = (float)(k0 - mh), db = (float)(k1 - mh);
         const float lb = fminf(fmaf(-da * da, c, zm), fmaf(-db * db, c, zm));
-        for (int j = 0; j < nch; ++j) {
+        for (int j = q; j < nch; j += kPlanQ) {
           const int clo = j * kCW, chi = min(clo + kCW, len) - 1;
           const int d = clo > k1 ? clo - k1 : (chi < k0 ? k0 - chi : 0);
           if (fmaf(-(float)d * (float)d, c, cm[j]) >= lb - kCut) {
-            if (wlo < 0) wlo = j;
-            whi = j;
+            wlo = min(wlo, j);
+            whi = max(whi, j);
           }
         }
       }
+#pragma unroll
+      for (int d = 1; d < kPlanQ; d <<= 1) {
+        wlo = min(wlo, __shfl_xor_sync(0xffffffffu, wlo, d));
+        whi = max(whi, __shfl_xor_sync(0xffffffffu, whi, d));
+      }
+      if (!has || q != 0) continue;
       const size_t pi = (size_t)t * a.plan_stride + row;
       if (alpha == -INFINITY) {                           // no finite term: empty row
         p_alpha[pi] = -INFINITY;
@@ -196,8 +275,8 @@ __global__ void __launch_bounds__(kPlanWarps * 32) band_plan_kernel(const __grid
   if (ext) {
     // the CTA's rows share one row block: one global atomic pair per tile
     __syncthreads();
-    const int rb = ((int)blockIdx.x * nwarps - a.plan_base) / 128;
-    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+    const int rb = (grow0 - a.plan_base) / 128;
+    for (int t = tid; t < T; t += blockDim.x) {
       if (s_uhi[t] > 0) {
         atomicMin(&a.ext_lo[rb * T + t], s_ulo[t]);
         atomicMax(&a.ext_hi[rb * T + t], s_uhi[t]);
@@ -257,15 +336,18 @@ void band_prepare(cudaStream_t s, BandTable<MAXP>& t) {
   int nch = 1;
   for (int q = 0; q < t.n; ++q) nch = std::max(nch, t.p[q].n_chunks);
   t.plan_row_stride = plan_row_floats(nch);
-  // rows per CTA: a power of two up to kPlanWarps (so that a CTA never straddles two problems
-  // or two 128-row blocks), as many as fit the default 48 KB of shared memory together with the
-  // per-tile unit extents
+  // warps per row: enough tile groups of eight for the widest row of tiles (at most 32); rows
+  // per CTA: a power of two up to 8 (a CTA never straddles two problems or two 128-row
+  // blocks) within 8 warps per CTA (or the row's own warps) and the default 48 KB of shared
+  // memory together with the per-tile unit extents
+  int wpr = std::max(1, std::min(32, (t.plan_tiles + kPlanTPW - 1) / kPlanTPW));
+  t.plan_wpr = wpr;
   const size_t tile_bytes = 2 * sizeof(int) * (size_t)t.plan_tiles;
-  int wpb = kPlanWarps;
-  while (wpb > 1 && wpb * t.plan_row_stride * sizeof(float) + tile_bytes > 48 * 1024) wpb /= 2;
-  const size_t smem = (size_t)wpb * t.plan_row_stride * sizeof(float) + tile_bytes;
+  int R = 8;
+  while (R > 1 && (R * wpr > std::max(8, wpr) || R * t.plan_row_stride * sizeof(float) + tile_bytes > 48 * 1024)) R /= 2;
+  const size_t smem = (size_t)R * t.plan_row_stride * sizeof(float) + tile_bytes;
   ktimer_begin(s, kKPlan);
-  band_plan_kernel<MAXP><<<t.plans / wpb, wpb * 32, smem, s>>>(t);
+  band_plan_kernel<MAXP><<<t.plans / R, R * wpr * 32, smem, s>>>(t);
   ktimer_end(s);
 }
 

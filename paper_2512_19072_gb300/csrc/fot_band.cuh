@@ -51,6 +51,7 @@ struct BandTable {
   int rows, plans, items, ctas;          // totals of the four work kinds (ctas: 128-row units)
   int plan_row_stride;                   // floats of plan-kernel shared memory per row
   int plan_tiles;                        // largest n_tiles of the table
+  int plan_wpr;                          // plan kernel: warps per row
   // tensor-core pass: chunk sums of units split between CTAs ([grid][slot_chunks][128][tile_w]
   // floats, indexed by the unit's first contributor) and the wait limit of the pipeline barriers
   float* slots;

@@ -22,7 +22,7 @@
 // arithmetic of every output is thus the same whatever the split (and whatever else shares the
 // launch, e.g. the other problems of a batch): results do not depend on the grid.
 //
-// Warp roles (704 threads):
+// Warp roles (832 threads):
 //  * warp 16, one lane (TMA): per stage, the 128 x 32 FP32 tile of x by a 2-D tensor copy
 //    (128-byte swizzle), at a unit's first stage also the 128 row offsets alpha (a 1-D bulk
 //    copy, once for the producers and once for the epilogue), and the stage's B operand (a
@@ -34,9 +34,10 @@
 //    A_hi x [B_hi | B_lo] (N = 2 TN) and A_lo x B_hi (N = TN) into an FP32 accumulator in
 //    tensor memory, so that hi*hi + hi*lo + lo*hi is accumulated (about 2^-16 relative per
 //    product instead of 2^-8); two accumulators alternate between consecutive units.
-//  * warps 18-21 (epilogue): read the accumulator (tcgen05.ld), add its two halves, take log2
-//    (MUFU lg2), add the offsets; the potential-update pass also applies
-//    f = eps (log a - S) with log a prefetched into shared memory.
+//  * warps 18-25 (epilogue, two per tensor-memory lane quarter, each with half of the tile's
+//    columns): read the accumulator (tcgen05.ld), add its two halves, take log2 (MUFU lg2),
+//    add the offsets; the potential-update pass also applies f = eps (log a - S) with log a
+//    prefetched into shared memory.
 // Every barrier wait is bounded: on time-out the kernel latches FOT_ETIMEOUT, all roles leave
 // their loops, the copies and MMAs in flight are waited for (again bounded) and the tensor
 // memory is freed.
@@ -62,15 +63,16 @@ namespace {
 constexpr int kTM = 128;                 // rows per unit (MMA M, TMEM lanes)
 constexpr int kKC = 32;                  // window positions per stage
 constexpr int kXStages = 4;              // x tiles in flight
-constexpr int kOpStages = 4;             // operand stages in flight
+constexpr int kOpStagesMax = 4;          // operand stages in flight (TcShape::kOpStages)
 constexpr int kAccBufs = 2;              // tensor-memory accumulators
 constexpr int kEpiAlpha = 4;             // epilogue copies of alpha in flight
 constexpr int kProdWarps = 16;
 constexpr int kProd = kProdWarps * 32;   // 512 producer threads
-constexpr int kTmaWarp = 16, kMmaWarp = 17, kEpiWarp0 = 18, kEpiWarps = 4;
-constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;   // 704
+constexpr int kTmaWarp = 16, kMmaWarp = 17, kEpiWarp0 = 18, kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;   // 832
 constexpr int kWarps = kThreads / 32;
-constexpr int kEpi = kEpiWarps * 32;     // 128 epilogue threads, one per accumulator row
+constexpr int kEpi = kEpiWarps * 32;     // 256 epilogue threads: two per accumulator row (the
+                                         // halves of the tile's columns)
 constexpr int kXBytes = kTM * kKC * 4;   // 16 KB x tile
 constexpr int kAlphaBytes = kTM * 4;     // 512 B of offsets
 constexpr int kABytes = kTM * kKC * 2;   // 8 KB per BF16 part of A
@@ -86,6 +88,10 @@ constexpr int kRouteKC = 64;             // window rounding of the host's tile-w
 // dynamic shared memory (bytes from a 1024-aligned base): the x ring, the producers' alpha per
 // x slot, the epilogue's alpha ring, the log-marginal prefetch, the operand ring
 template <int TN> struct TcShape {
+  // operand stages in flight: four, three for 64-wide tiles (with four, repeated identical
+  // 64-wide passes gave results that differed from run to run in some units, a pipeline race
+  // whose cause was not found; three stages gave identical results in every test)
+  static constexpr int kOpStages = TN == 64 ? 3 : kOpStagesMax;
   static constexpr int kBBytes = 2 * TN * kKC * 2;          // B_hi rows, then B_lo rows
   static constexpr int kOpBytes = 2 * kABytes + kBBytes;
   static constexpr int kXAlphaOff = kXStages * kXBytes;
@@ -152,12 +158,27 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
+// the same with a suspend-time hint: the thread may sleep up to hint_ns until the phase
+// completes instead of spinning (its warp then takes no issue slots from the others)
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t mbar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(mbar), "r"(parity), "r"(hint_ns) : "memory");
+  return ok != 0;
+}
+
+constexpr uint32_t kSleepNs = 2000;      // suspend-time hint of a poll (normal wait limit only)
+
 // Bounded wait.  Returns false when another role has aborted the CTA, or when `limit` polls
-// pass (then FOT_ETIMEOUT is latched and the CTA aborted).
+// pass (then FOT_ETIMEOUT is latched and the CTA aborted).  With the normal limit each poll
+// may sleep up to kSleepNs; a shorter limit (the test setting) polls without sleeping.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit, int* err,
                                           volatile int* abort) {
+  const bool sleep = limit >= kSpinDefault;
   for (int i = 0; i < limit; ++i) {
-    if (mbar_try(mbar, parity)) return true;
+    if (sleep ? mbar_try_sleep(mbar, parity, kSleepNs) : mbar_try(mbar, parity)) return true;
     if ((i & 31) == 31 && *abort) return false;
   }
   raise_error(err, FOT_ETIMEOUT);
@@ -211,6 +232,34 @@ __device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p
   *reinterpret_cast<uint4*>(lo_p) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+// tensor-memory load / store of N consecutive 32-bit columns of this warp's 32 lanes
+template <int N> __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
+template <> __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+template <int N> __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* v);
+template <> __device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+template <> __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+      :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
 // the CTA holding stage x of the pass when S stages are shared out over C CTAs (CTA k takes
 // [k S / C, (k + 1) S / C))
 __device__ __forceinline__ int cta_of(long long x, long long S, int C) {
@@ -219,7 +268,9 @@ __device__ __forceinline__ int cta_of(long long x, long long S, int C) {
 __device__ __forceinline__ long long share_start(int k, long long S, int C) { return (long long)k * S / C; }
 
 // what a unit needs: its stage count when it takes the tensor cores (0 otherwise), whether it
-// takes the CUDA-core sums instead, its union window start
+// takes the CUDA-core sums instead, its union window start.  Every CTA must derive the same
+// partition, so nothing here may change while the kernel runs (the error latch, which another
+// CTA may set meanwhile, is not consulted).
 template <int TN, int MAXP>
 __device__ __forceinline__ void unit_info(const BandTable<MAXP>& tab, int u, int& S, int& decl, int& lo) {
   const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, u)];
@@ -228,10 +279,9 @@ __device__ __forceinline__ void unit_info(const BandTable<MAXP>& tab, int u, int
   const int hi = a.ext_hi[lu];
   const int W = hi > lo ? (hi - lo + kKC - 1) / kKC * kKC : 0;
   const float kmax = (float)(TN / 2);
-  const bool latched = error_latched(a.err);
-  const bool take = !latched && W > 0 && kmax * (float)W * a.c <= kTiltMaxTC && kmax * kmax * a.c <= 32.f;
+  const bool take = W > 0 && kmax * (float)W * a.c <= kTiltMaxTC && kmax * kmax * a.c <= 32.f;
   S = take ? W / kKC : 0;
-  decl = (!latched && !take) ? 1 : 0;
+  decl = take ? 0 : 1;
 }
 
 // CUDA-core window sums of a unit outside the tensor path: 16-row items, the tile's 16-wide
@@ -258,13 +308,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t xfull[kXStages], xempty[kXStages];
-  __shared__ uint64_t opfull[kOpStages], opempty[kOpStages], bfull[kOpStages];
+  __shared__ uint64_t opfull[Sh::kOpStages], opempty[Sh::kOpStages], bfull[Sh::kOpStages];
   __shared__ uint64_t accfull[kAccBufs], accempty[kAccBufs];
   __shared__ uint64_t eafull[kEpiAlpha], eaempty[kEpiAlpha];
   __shared__ uint64_t drain;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_np, s_nd, s_first, s_last;
   __shared__ int4 s_piece[kMaxPieces];   // unit, first stage of the unit in the pass, stages, lo
+  __shared__ int4 s_pcon[kMaxPieces];    // first and last contributor CTA, contributors
   __shared__ int s_decl[kMaxDecl];
   __shared__ long long s_wsum[kWarps][2];
 
@@ -290,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       mbar_init(smem_u32(&xfull[i]), 1);
       mbar_init(smem_u32(&xempty[i]), kProd);
     }
-    for (int i = 0; i < kOpStages; ++i) {
+    for (int i = 0; i < Sh::kOpStages; ++i) {
       mbar_init(smem_u32(&opfull[i]), kProd);
       mbar_init(smem_u32(&opempty[i]), 1);
       mbar_init(smem_u32(&bfull[i]), 1);
@@ -383,6 +434,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
           const int idx = (int)(R - s_first);
           if (idx >= 0 && idx < kMaxPieces) {
             s_piece[idx] = make_int4(u0 + i, (int)P, uS[i], uL[i]);
+            // contributors: the distinct CTAs holding a chunk start of the unit (a share
+            // shorter than a chunk can hold none)
+            const int nc = (uS[i] + kChunk - 1) / kChunk;
+            int ncon = 0, prev = -1;
+            for (int jj = 0; jj < nc; ++jj) {
+              const int k = cta_of(P + (long long)jj * kChunk, S_tot, C);
+              if (k != prev) {
+                ++ncon;
+                prev = k;
+              }
+            }
+            s_pcon[idx] = make_int4(cta_of(P, S_tot, C), prev, ncon, 0);
             atomicMax(&s_np, idx + 1);
           } else {
             raise_error(err0, FOT_EUNSUPPORTED);
@@ -411,13 +474,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 
   // piece i: unit, its chunks [jlo, jhi) here (stages [b, e)), whether it is split, and the
   // first contributor (whose index names the split unit's slots)
+  // (the problem's fields are copied into the piece once: read through a pointer into the
+  // kernel's parameters they would be reloaded after every barrier operation)
   struct Piece {
     const BandArgs* a;
-    int lu, r0, tile, k0, kc, lo, S, nc, jlo, jhi, b, e, P, ca, cb;
+    int lu, r0, tile, k0, kc, lo, S, nc, jlo, jhi, b, e, P, ca, ncon;
     bool split;
+    int* err;
+    int len, n_rows;
+    float c, sc, eps;
   };
   auto piece = [&](int i) {
     const int4 q = s_piece[i];
+    const int4 con = s_pcon[i];
     Piece p;
     p.a = &tab.p[find_prob<MAXP, 3>(tab, q.x)];
     p.lu = q.x - p.a->cta_base;
@@ -432,9 +501,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     chunks_here(q.y, q.z, p.jlo, p.jhi);
     p.b = p.jlo * kChunk;
     p.e = min(p.jhi * kChunk, p.S);
-    p.ca = cta_of(q.y, S_tot, C);
-    p.cb = cta_of((long long)q.y + (long long)(p.nc - 1) * kChunk, S_tot, C);
-    p.split = p.ca != p.cb;
+    p.ca = con.x;
+    p.ncon = con.z;
+    p.split = con.x != con.y;
+    p.err = p.a->err;
+    p.len = p.a->len;
+    p.n_rows = p.a->n_rows;
+    p.c = p.a->c;
+    p.sc = p.a->x_scale;
+    p.eps = p.a->eps;
     return p;
   };
 
@@ -454,27 +529,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         const Piece p = piece(i);
         const BandArgs& a = *p.a;
         const float* alpha_src = a.plan + (size_t)p.tile * a.plan_stride + p.r0;
+        const unsigned char* btab = a.btab + (size_t)(a.s_max - p.S) * Sh::kBBytes;
+        const void* xmap = a.xmap;
         for (int ch = p.b; ch < p.e && ok; ++ch) {
           const int s = xi % kXStages;
-          if (xi >= kXStages && !(ok = mbar_wait(smem_u32(&xempty[s]), ((xi / kXStages) - 1) & 1, spin, a.err, abort_flag))) break;
+          if (xi >= kXStages && !(ok = mbar_wait(smem_u32(&xempty[s]), ((xi / kXStages) - 1) & 1, spin, p.err, abort_flag))) break;
           const bool first = ch == p.b;
           mbar_expect_tx(smem_u32(&xfull[s]), kXBytes + (first ? kAlphaBytes : 0));
-          tma_load_2d(smem_u32(xring + s * kXBytes), a.xmap, p.lo + ch * kKC, p.r0, smem_u32(&xfull[s]));
+          tma_load_2d(smem_u32(xring + s * kXBytes), xmap, p.lo + ch * kKC, p.r0, smem_u32(&xfull[s]));
           if (first) bulk_load(smem_u32(xalpha + s * kAlphaBytes), alpha_src, kAlphaBytes, smem_u32(&xfull[s]));
           ++xi;
           issued_x = xi;
           if (first) {
             const int ea = i % kEpiAlpha;
-            if (i >= kEpiAlpha && !(ok = mbar_wait(smem_u32(&eaempty[ea]), ((i / kEpiAlpha) - 1) & 1, spin, a.err, abort_flag))) break;
+            if (i >= kEpiAlpha && !(ok = mbar_wait(smem_u32(&eaempty[ea]), ((i / kEpiAlpha) - 1) & 1, spin, p.err, abort_flag))) break;
             mbar_expect_tx(smem_u32(&eafull[ea]), kAlphaBytes);
             bulk_load(smem_u32(ealpha + ea * kAlphaBytes), alpha_src, kAlphaBytes, smem_u32(&eafull[ea]));
             issued_ea = i + 1;
           }
-          const int so = oi % kOpStages;
-          if (oi >= kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / kOpStages) - 1) & 1, spin, a.err, abort_flag))) break;
+          const int so = oi % Sh::kOpStages;
+          if (oi >= Sh::kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / Sh::kOpStages) - 1) & 1, spin, p.err, abort_flag))) break;
           mbar_expect_tx(smem_u32(&bfull[so]), Sh::kBBytes);
-          const int e_idx = 2 * ch - p.S + a.s_max;
-          bulk_load(smem_u32(opring + so * Sh::kOpBytes + 2 * kABytes), a.btab + (size_t)e_idx * Sh::kBBytes,
+          bulk_load(smem_u32(opring + so * Sh::kOpBytes + 2 * kABytes), btab + (size_t)(2 * ch) * Sh::kBBytes,
                     Sh::kBBytes, smem_u32(&bfull[so]));
           ++oi;
           issued_o = oi;
@@ -492,15 +568,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         for (int j = p.jlo; j < p.jhi && ok; ++j) {
           // chunk j: a fresh accumulator over its stages
           const int ab = ai % kAccBufs;
-          if (ai >= kAccBufs && !(ok = mbar_wait(smem_u32(&accempty[ab]), ((ai / kAccBufs) - 1) & 1, spin, p.a->err, abort_flag))) break;
+          if (ai >= kAccBufs && !(ok = mbar_wait(smem_u32(&accempty[ab]), ((ai / kAccBufs) - 1) & 1, spin, p.err, abort_flag))) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t dcol = tmem + (uint32_t)(ab * 2 * TN);
           const int s0 = j * kChunk, s1 = min(s0 + kChunk, p.S);
           for (int ch = s0; ch < s1; ++ch) {
-            const int so = oi % kOpStages;
-            const uint32_t par = (oi / kOpStages) & 1;
-            if (!(ok = mbar_wait(smem_u32(&opfull[so]), par, spin, p.a->err, abort_flag))) break;
-            if (!(ok = mbar_wait(smem_u32(&bfull[so]), par, spin, p.a->err, abort_flag))) break;
+            const int so = oi % Sh::kOpStages;
+            const uint32_t par = (oi / Sh::kOpStages) & 1;
+            if (!(ok = mbar_wait(smem_u32(&opfull[so]), par, spin, p.err, abort_flag))) break;
+            if (!(ok = mbar_wait(smem_u32(&bfull[so]), par, spin, p.err, abort_flag))) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = smem_u32(opring + so * Sh::kOpBytes);
             const uint32_t sAhi = st, sAlo = st + kABytes, sB = st + 2 * kABytes;
@@ -534,20 +610,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     bool ok = true;
     for (int i = 0; i < np && ok; ++i) {
       const Piece p = piece(i);
-      const BandArgs& a = *p.a;
-      const float c = a.c, sc = a.x_scale;
-      const bool rowok = p.r0 + ar < a.n_rows;
+      const float c = p.c, sc = p.sc;
+      const int len = p.len;
+      const bool rowok = p.r0 + ar < p.n_rows;
       float alpha = -INFINITY;
       for (int ch = p.b; ch < p.e; ++ch) {
         const int s = xi % kXStages;
-        if (!(ok = mbar_wait(smem_u32(&xfull[s]), (xi / kXStages) & 1, spin, a.err, abort_flag))) break;
+        if (!(ok = mbar_wait(smem_u32(&xfull[s]), (xi / kXStages) & 1, spin, p.err, abort_flag))) break;
         if (ch == p.b && rowok) alpha = reinterpret_cast<const float*>(xalpha + s * kAlphaBytes)[ar];
         const float4 x0 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc0);
         const float4 x1 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc1);
         mbar_arrive(smem_u32(&xempty[s]));
         ++xi;
-        const int so = oi % kOpStages;
-        if (oi >= kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / kOpStages) - 1) & 1, spin, a.err, abort_flag))) break;
+        const int so = oi % Sh::kOpStages;
+        if (oi >= Sh::kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / Sh::kOpStages) - 1) & 1, spin, p.err, abort_flag))) break;
         unsigned char* const stp = opring + so * Sh::kOpBytes;
         float v[8];
         const int m0 = p.lo + ch * kKC + aq * 8;         // absolute position of v[0]
@@ -562,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const float K = fmaf(Q, (float)j, fmaf(-(float)(j * j), c, P));
-            v[j] = (m0 + j < a.len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
+            v[j] = (m0 + j < len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
           }
         }
         store_split8(v, stp + aoff, stp + kABytes + aoff);
@@ -573,8 +649,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int q4 = warp & 3;                              // tensor-memory lane quarter
+    // two warps per tensor-memory lane quarter (warp % 4), each taking half of the columns
+    constexpr int HN = TN / 2;                            // columns of this thread
+    constexpr int CH = HN < 16 ? HN : 16;                 // columns per tensor-memory load
+    const int q4 = warp & 3;
+    const int hcol = ((warp - kEpiWarp0) >> 2) * HN;      // first column of this thread's half
     const int rl = 32 * q4 + lane;                        // accumulator row
+    const bool lead = rl == 0 && hcol == 0;               // one thread per CTA for the counters
     const uint32_t tlane = tmem + ((uint32_t)(32 * q4) << 16);
     const uint32_t tfold = tlane + (uint32_t)(4 * TN);    // running sum of the unit's chunks
     int ai = 0;
@@ -582,55 +663,62 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     for (int i = 0; i < np && ok; ++i) {
       const Piece p = piece(i);
       const BandArgs& a = *p.a;
+      const int n_rows = p.n_rows;
       const int row = p.r0 + rl;
-      const bool rowok = row < a.n_rows;
-      const int k1 = min(p.k0 + TN, a.len) - 1;
-      // the potential-update pass: log a of this row's outputs, into shared memory (each thread
-      // loads its own row; across the warp the loads of one output are contiguous)
+      const bool rowok = row < n_rows;
+      const int k1 = min(p.k0 + TN, p.len) - 1;
+      float* const y = a.y;
+      float* const logsum = a.logsum;
+      const float* const lmarg = a.lmarg;
+      int* const err = p.err;
+      const float peps = p.eps;
+      // the potential-update pass: log a of this thread's outputs, into shared memory (each
+      // thread loads its own row; across the warp the loads of one output are contiguous)
       if (MODE == 1 && rowok) {
-        for (int n = 0; n < TN; ++n) {
+        for (int n = hcol; n < hcol + HN; ++n) {
           const int k = min(p.k0 + n, k1);
           const uint32_t dst = smem_u32(s_lm + n * kTM + rl);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(a.lmarg + (size_t)k * a.n_rows + row) : "memory");
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(lmarg + (size_t)k * n_rows + row) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
       }
       const int ea = i % kEpiAlpha;
-      ok = mbar_wait(smem_u32(&eafull[ea]), (i / kEpiAlpha) & 1, spin, a.err, abort_flag);
+      ok = mbar_wait(smem_u32(&eafull[ea]), (i / kEpiAlpha) & 1, spin, err, abort_flag);
       float alpha = -INFINITY;
       if (ok) {
         if (rowok) alpha = reinterpret_cast<const float*>(ealpha + ea * kAlphaBytes)[rl];
         mbar_arrive(smem_u32(&eaempty[ea]));
       }
-      if (!epi_all(ok)) break;                            // the same for all 128 threads
-      if (rl == 0) atomicAdd(a.tc_terms, (unsigned long long)(p.e - p.b) * kKC * TN * kTM);
-      const float c = a.c;
+      if (!epi_all(ok)) break;                            // the same for all epilogue threads
+      if (lead) atomicAdd(a.tc_terms, (unsigned long long)(p.e - p.b) * kKC * TN * kTM);
+      const float c = p.c;
       const float mref = (float)p.lo + 0.5f * (float)(p.S * kKC);
+      // the tilt of output column n: alpha + 2 (n - TN/2) (mref - kc) c
+      const float tilt0 = fmaf(2.f * (float)(-TN / 2) * (mref - (float)p.kc), c, alpha);
+      const float tstep = 2.f * (mref - (float)p.kc) * c;
       bool lm_ready = false;
-      // outputs (o = k0 + c0 + u, r = row) from 16 sums
-      auto emit = [&](int c0, const float* cv16) {
+      // outputs (o = k0 + c0 + u, r = row) from CH sums
+      auto emit = [&](int c0, const float* cv) {
         if (!rowok) return;
         if (MODE == 1 && !lm_ready) {
           asm volatile("cp.async.wait_all;" ::: "memory");
           lm_ready = true;
         }
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < CH; ++u) {
           const int n = c0 + u;
           const int k = p.k0 + n;
           if (k > k1) break;
-          const float kap = (float)(n - TN / 2);
-          const float cv = cv16[u];
           float out = -INFINITY;
           if (alpha != -INFINITY) {
-            if (cv > 0.f && isfinite(cv))
-              out = __fadd_rn(fmaf(2.f * kap * (mref - (float)p.kc), c, alpha), lg2(cv));
+            if (cv[u] > 0.f && cv[u] <= 3.4e38f)
+              out = __fadd_rn(fmaf((float)n, tstep, tilt0), lg2(cv[u]));
             else
-              raise_error(a.err, FOT_ENONFINITE);
+              raise_error(err, FOT_ENONFINITE);
           }
-          const size_t yi = (size_t)k * a.n_rows + row;
+          const size_t yi = (size_t)k * n_rows + row;
           if (MODE == 0) {
-            a.y[yi] = out;
+            y[yi] = out;
           } else {
             const float sv = __fmul_rn(out, kLn2);
             const float lm = s_lm[n * kTM + rl];
@@ -638,17 +726,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             if (lm == -INFINITY) {
               pot = -INFINITY;
             } else {
-              pot = __fmul_rn(a.eps, __fsub_rn(lm, sv));
-              if (!isfinite(pot)) raise_error(a.err, FOT_ENONFINITE);
+              pot = __fmul_rn(peps, __fsub_rn(lm, sv));
+              if (!isfinite(pot)) raise_error(err, FOT_ENONFINITE);
             }
-            a.y[yi] = pot;
-            if (a.logsum) a.logsum[yi] = sv;
+            y[yi] = pot;
+            if (logsum) logsum[yi] = sv;
           }
         }
       };
       for (int j = p.jlo; j < p.jhi; ++j) {
         const int ab = ai % kAccBufs;
-        ok = mbar_wait(smem_u32(&accfull[ab]), (ai / kAccBufs) & 1, spin, a.err, abort_flag);
+        ok = mbar_wait(smem_u32(&accfull[ab]), (ai / kAccBufs) & 1, spin, err, abort_flag);
         if (!epi_all(ok)) {
           ok = false;
           break;
@@ -656,53 +744,37 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t tacc = tlane + (uint32_t)(ab * 2 * TN);
         const bool last = j == p.nc - 1;
-        // chunk sum = D[0:TN) + D[TN:2TN) (the three split products), 16 columns at a time; a
+        // chunk sum = D[0:TN) + D[TN:2TN) (the three split products), CH columns at a time; a
         // split unit's chunk sums go to its slots, the others are added to the running sum
         float* slot = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN;
 #pragma unroll
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-          uint32_t d1[16], d2[16];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(d1[0]), "=r"(d1[1]), "=r"(d1[2]), "=r"(d1[3]), "=r"(d1[4]), "=r"(d1[5]), "=r"(d1[6]), "=r"(d1[7]),
-                "=r"(d1[8]), "=r"(d1[9]), "=r"(d1[10]), "=r"(d1[11]), "=r"(d1[12]), "=r"(d1[13]), "=r"(d1[14]), "=r"(d1[15])
-              : "r"(tacc + (uint32_t)c0));
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(d2[0]), "=r"(d2[1]), "=r"(d2[2]), "=r"(d2[3]), "=r"(d2[4]), "=r"(d2[5]), "=r"(d2[6]), "=r"(d2[7]),
-                "=r"(d2[8]), "=r"(d2[9]), "=r"(d2[10]), "=r"(d2[11]), "=r"(d2[12]), "=r"(d2[13]), "=r"(d2[14]), "=r"(d2[15])
-              : "r"(tacc + (uint32_t)(TN + c0)));
+        for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
+          uint32_t d1[CH], d2[CH];
+          tmem_ld<CH>(tacc + (uint32_t)c0, d1);
+          tmem_ld<CH>(tacc + (uint32_t)(TN + c0), d2);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          float cv[16];
+          float cv[CH];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) cv[u] = __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
+          for (int u = 0; u < CH; ++u) cv[u] = __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
           if (p.split) {
 #pragma unroll
-            for (int u = 0; u < 16; u += 4)
+            for (int u = 0; u < CH; u += 4)
               *reinterpret_cast<float4*>(slot + c0 + u) = make_float4(cv[u], cv[u + 1], cv[u + 2], cv[u + 3]);
           } else {
             if (j > 0) {                                  // running sum of chunks 0 .. j-1
-              uint32_t f[16];
-              asm volatile(
-                  "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                  : "=r"(f[0]), "=r"(f[1]), "=r"(f[2]), "=r"(f[3]), "=r"(f[4]), "=r"(f[5]), "=r"(f[6]), "=r"(f[7]),
-                    "=r"(f[8]), "=r"(f[9]), "=r"(f[10]), "=r"(f[11]), "=r"(f[12]), "=r"(f[13]), "=r"(f[14]), "=r"(f[15])
-                  : "r"(tfold + (uint32_t)c0));
+              uint32_t f[CH];
+              tmem_ld<CH>(tfold + (uint32_t)c0, f);
               asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-              for (int u = 0; u < 16; ++u) cv[u] = __uint_as_float(f[u]) + cv[u];
+              for (int u = 0; u < CH; ++u) cv[u] = __uint_as_float(f[u]) + cv[u];
             }
             if (last) {
               emit(c0, cv);
             } else {
-              asm volatile(
-                  "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-                  :: "r"(tfold + (uint32_t)c0),
-                     "r"(__float_as_uint(cv[0])), "r"(__float_as_uint(cv[1])), "r"(__float_as_uint(cv[2])), "r"(__float_as_uint(cv[3])),
-                     "r"(__float_as_uint(cv[4])), "r"(__float_as_uint(cv[5])), "r"(__float_as_uint(cv[6])), "r"(__float_as_uint(cv[7])),
-                     "r"(__float_as_uint(cv[8])), "r"(__float_as_uint(cv[9])), "r"(__float_as_uint(cv[10])), "r"(__float_as_uint(cv[11])),
-                     "r"(__float_as_uint(cv[12])), "r"(__float_as_uint(cv[13])), "r"(__float_as_uint(cv[14])), "r"(__float_as_uint(cv[15]))
-                  : "memory");
+              uint32_t f[CH];
+#pragma unroll
+              for (int u = 0; u < CH; ++u) f[u] = __float_as_uint(cv[u]);
+              tmem_st<CH>(tfold + (uint32_t)c0, f);
             }
           }
         }
@@ -714,32 +786,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       if (!ok) break;
       if (p.split) {
         // the last contributor adds all chunk sums of the unit in chunk order (the same sums,
-        // in the same order, as an unsplit unit) and writes the outputs
-        __threadfence();
+        // in the same order, as an unsplit unit) and writes the outputs.  (The grid
+        // synchronisation pattern: the epilogue's writes are gathered by the barrier, one
+        // thread publishes them with a device-scope fence before the count and fences again
+        // after reading the final count, before the barrier that releases the readers.)
         asm volatile("bar.sync 1, %0;" :: "r"(kEpi) : "memory");
-        if (rl == 0) {
-          // contributors: the distinct CTAs holding a chunk start of the unit (a share shorter
-          // than a chunk can hold none)
-          int ncon = 0, prev = -1;
-          for (int j = 0; j < p.nc; ++j) {
-            const int k = cta_of((long long)p.P + (long long)j * kChunk, S_tot, C);
-            if (k != prev) {
-              ++ncon;
-              prev = k;
-            }
-          }
-          s_last = atomicAdd(&a.ucnt[p.lu], 1) == ncon - 1;
+        if (lead) {
+          __threadfence();
+          s_last = atomicAdd(&a.ucnt[p.lu], 1) == p.ncon - 1;
+          __threadfence();
         }
         asm volatile("bar.sync 1, %0;" :: "r"(kEpi) : "memory");
         if (s_last) {
-          __threadfence();
 #pragma unroll
-          for (int c0 = 0; c0 < TN; c0 += 16) {
-            float cv[16];
+          for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
+            float cv[CH];
             for (int j = 0; j < p.nc; ++j) {
               const float* sl = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN + c0;
 #pragma unroll
-              for (int u = 0; u < 16; u += 4) {
+              for (int u = 0; u < CH; u += 4) {
                 const float4 t4 = __ldcg(reinterpret_cast<const float4*>(sl + u));
                 if (j == 0) {
                   cv[u] = t4.x;
@@ -756,14 +821,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             }
             emit(c0, cv);
           }
-          if (rl == 0) a.ucnt[p.lu] = 0;
+          if (lead) a.ucnt[p.lu] = 0;
         }
       }
+      // the log-marginal prefetch lands before the next piece reuses its buffer
+      if (MODE == 1 && rowok) asm volatile("cp.async.wait_all;" ::: "memory");
     }
   }
 
   // ---- units outside the tensor path: CUDA-core window sums by the producer warps ------------
-  // (every x tile has been consumed, so the x ring is free as scratch)
+  // The x ring serves as their scratch once every producer warp has read its last x tile (a
+  // barrier of the producer warps: a warp that finishes early must not overwrite a tile that
+  // another warp still reads).
+  if (warp < kProdWarps) asm volatile("bar.sync 3, %0;" :: "r"(kProd) : "memory");
   if (warp < kProdWarps && !*abort_flag) {
     float* sAw = reinterpret_cast<float*>(xring) + warp * 2 * kSA;
     for (int d = 0; d < nd; ++d) {
@@ -782,8 +852,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     if (warp == kTmaWarp && lane == 0) {
       for (int s = 0; s < kXStages && s < issued_x; ++s)
         mbar_drain(smem_u32(&xfull[s]), ((issued_x - 1 - s) / kXStages) & 1);
-      for (int s = 0; s < kOpStages && s < issued_o; ++s)
-        mbar_drain(smem_u32(&bfull[s]), ((issued_o - 1 - s) / kOpStages) & 1);
+      for (int s = 0; s < Sh::kOpStages && s < issued_o; ++s)
+        mbar_drain(smem_u32(&bfull[s]), ((issued_o - 1 - s) / Sh::kOpStages) & 1);
       for (int s = 0; s < kEpiAlpha && s < issued_ea; ++s)
         mbar_drain(smem_u32(&eafull[s]), ((issued_ea - 1 - s) / kEpiAlpha) & 1);
     }
@@ -791,7 +861,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       mma_commit(smem_u32(&drain));
       mbar_drain(smem_u32(&drain), 0);
     }
-    if (tid < kEpi + kEpiWarp0 * 32 && tid >= kEpiWarp0 * 32 && MODE == 1)
+    if (warp >= kEpiWarp0 && MODE == 1)
       asm volatile("cp.async.wait_all;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

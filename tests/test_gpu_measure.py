@@ -28,8 +28,12 @@ def test_kernel_times_cover_the_loop(fot_lib, prec):
     assert 0.0 < ms <= loop_ms * 1.001 + 1e-3, (ms, loop_ms)
     if prec == "dense":
         assert times["axis_pass_kernel"][1] == 4 * w.iters
-    else:
+    elif prec == "fp32":
         assert times["band_plan_kernel"][1] == 4 * w.iters
+    else:
+        # the plan class also holds the B-operand table writes: one whenever eps changes
+        n_eps = len(set(np.asarray(w.eps, dtype=float).tolist()))
+        assert 4 * w.iters < times["band_plan_kernel"][1] <= 4 * w.iters + n_eps
     # the sums reset on reading; a second solve is timed alone
     assert sum(n for _, n in B.fot_kernel_times(ctx).values()) == 0
     B.fot_solve(ctx, g, G, w.eps, w.iters)
