@@ -38,7 +38,9 @@ struct BandArgs {
   int s_max;           // B table: window stages of the longest possible window (len / 32 up)
   int row_base, plan_base, item_base, cta_base;   // first global work index of each kernel
   int plan_rows;       // rows of the plan kernel's grid for this problem (n_rows rounded up to 8)
+  int lm_tma;          // potential-update tensor pass: lmap holds lmarg (else read directly)
   alignas(64) unsigned char xmap[128];   // CUtensorMap of x for the tensor-core pass
+  alignas(64) unsigned char lmap[128];   // CUtensorMap of lmarg (potential-update tensor pass)
 };
 
 constexpr int kMaxBatch = 64;
@@ -59,6 +61,7 @@ struct BandTable {
   int spin_limit;
   BandArgs p[MAXP];
 };
+static_assert(sizeof(BandTable<kMaxBatch>) <= 32764, "kernel parameter limit");
 
 // problem owning global work index gi of kind WHICH (0 rows, 1 plan rows, 2 band items,
 // 3 tensor-core units): binary search over the prefix sums (a single problem needs none)

@@ -22,22 +22,22 @@
 // arithmetic of every output is thus the same whatever the split (and whatever else shares the
 // launch, e.g. the other problems of a batch): results do not depend on the grid.
 //
-// Warp roles (832 threads):
-//  * warp 16, one lane (TMA): per stage, the 128 x 32 FP32 tile of x by a 2-D tensor copy
-//    (128-byte swizzle), at a unit's first stage also the 128 row offsets alpha (a 1-D bulk
-//    copy, once for the producers and once for the epilogue), and the stage's B operand (a
-//    1-D bulk copy from the pass's B table).
-//  * warps 0-15 (producers): thread (row ar, quarter aq) turns its 8 window positions into A,
+// Warp roles (576 threads):
+//  * warp 8, one lane (TMA): per stage, the 128 x 32 FP32 tile of x by a 2-D tensor copy
+//    (128-byte swizzle) and the stage's B operand (a 1-D bulk copy from the pass's B table); at
+//    a unit's first stage also the 128 row offsets alpha (1-D bulk copies for the producers and
+//    for the epilogue) and, in the potential-update pass, the unit's [TN][128] block of log a
+//    (a 2-D tensor copy) into the epilogue's slot.
+//  * warps 0-7 (producers): thread (row ar, half ah) turns its 16 window positions into A,
 //    split into two BF16 parts (v = hi + lo), stored in the canonical K-major core-matrix
 //    layout.
-//  * warp 17, one lane (MMA): per 16-position K step two tcgen05.mma (kind::f16, M = 128):
+//  * warp 9, one lane (MMA): per 16-position K step two tcgen05.mma (kind::f16, M = 128):
 //    A_hi x [B_hi | B_lo] (N = 2 TN) and A_lo x B_hi (N = TN) into an FP32 accumulator in
 //    tensor memory, so that hi*hi + hi*lo + lo*hi is accumulated (about 2^-16 relative per
-//    product instead of 2^-8); two accumulators alternate between consecutive units.
-//  * warps 18-25 (epilogue, two per tensor-memory lane quarter, each with half of the tile's
+//    product instead of 2^-8); two accumulators alternate between consecutive chunks.
+//  * warps 10-17 (epilogue, two per tensor-memory lane quarter, each with half of the tile's
 //    columns): read the accumulator (tcgen05.ld), add its two halves, take log2 (MUFU lg2),
-//    add the offsets; the potential-update pass also applies f = eps (log a - S) with log a
-//    prefetched into shared memory.
+//    add the offsets; the potential-update pass also applies f = eps (log a - S).
 // Every barrier wait is bounded: on time-out the kernel latches FOT_ETIMEOUT, all roles leave
 // their loops, the copies and MMAs in flight are waited for (again bounded) and the tensor
 // memory is freed.
@@ -65,11 +65,11 @@ constexpr int kKC = 32;                  // window positions per stage
 constexpr int kXStages = 4;              // x tiles in flight
 constexpr int kOpStagesMax = 4;          // operand stages in flight (TcShape::kOpStages)
 constexpr int kAccBufs = 2;              // tensor-memory accumulators
-constexpr int kEpiAlpha = 4;             // epilogue copies of alpha in flight
-constexpr int kProdWarps = 16;
-constexpr int kProd = kProdWarps * 32;   // 512 producer threads
-constexpr int kTmaWarp = 16, kMmaWarp = 17, kEpiWarp0 = 18, kEpiWarps = 8;
-constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;   // 832
+constexpr int kEpiBufs = 2;              // epilogue slots in flight (a unit's alpha and log a)
+constexpr int kProdWarps = 8;
+constexpr int kProd = kProdWarps * 32;   // 256 producer threads
+constexpr int kTmaWarp = 8, kMmaWarp = 9, kEpiWarp0 = 10, kEpiWarps = 8;
+constexpr int kThreads = (kEpiWarp0 + kEpiWarps) * 32;   // 576
 constexpr int kWarps = kThreads / 32;
 constexpr int kEpi = kEpiWarps * 32;     // 256 epilogue threads: two per accumulator row (the
                                          // halves of the tile's columns)
@@ -86,19 +86,21 @@ constexpr int kSpinDefault = 1 << 20;    // bounded mbarrier polls
 constexpr int kRouteKC = 64;             // window rounding of the host's tile-width estimate
 
 // dynamic shared memory (bytes from a 1024-aligned base): the x ring, the producers' alpha per
-// x slot, the epilogue's alpha ring, the log-marginal prefetch, the operand ring
+// x slot, the epilogue's ring (per slot a unit's alpha, then in the potential-update pass its
+// [TN][128] block of log a), the operand ring
 template <int TN> struct TcShape {
-  // operand stages in flight: four, three for 64-wide tiles (with four, repeated identical
-  // 64-wide passes gave results that differed from run to run in some units, a pipeline race
-  // whose cause was not found; three stages gave identical results in every test)
+  // operand stages in flight: four, three for 64-wide tiles (four do not fit in shared memory
+  // beside the epilogue's two slots of log a)
   static constexpr int kOpStages = TN == 64 ? 3 : kOpStagesMax;
   static constexpr int kBBytes = 2 * TN * kKC * 2;          // B_hi rows, then B_lo rows
   static constexpr int kOpBytes = 2 * kABytes + kBBytes;
   static constexpr int kXAlphaOff = kXStages * kXBytes;
-  static constexpr int kEAlphaOff = kXAlphaOff + kXStages * kAlphaBytes;
-  static constexpr int kLmOff = kEAlphaOff + kEpiAlpha * kAlphaBytes;
-  static constexpr int kOpOff = kLmOff + TN * kTM * 4;
+  static constexpr int kEpiOff = kXAlphaOff + kXStages * kAlphaBytes;
+  static constexpr int kLmBytes = TN * kTM * 4;
+  static constexpr int kEpiSlot = kAlphaBytes + kLmBytes;
+  static constexpr int kOpOff = kEpiOff + kEpiBufs * kEpiSlot;
   static constexpr int kSmemBytes = kOpOff + kOpStages * kOpBytes + 1024;
+  static_assert(kSmemBytes <= 227 * 1024 - 8 * 1024, "shared memory per CTA (dynamic + static)");
   // 2 accumulators of 2TN columns, then the TN-column running sum of a unit's chunks
   static constexpr uint32_t kTmemCols = 5 * TN <= 32 ? 32 : 5 * TN <= 64 ? 64 : 5 * TN <= 128 ? 128 : 5 * TN <= 256 ? 256 : 512;
 };
@@ -246,6 +248,29 @@ template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr));
 }
+// Wait for this thread's tensor-memory loads and pin their destination registers: the
+// registers pass through the wait as read-write operands, so no use of them can be scheduled
+// before the wait (a "memory" clobber orders memory accesses only, not register arithmetic).
+template <int N> __device__ __forceinline__ void reg_pin(uint32_t* v);
+template <> __device__ __forceinline__ void reg_pin<8>(uint32_t* v) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]) :: "memory");
+}
+template <> __device__ __forceinline__ void reg_pin<16>(uint32_t* v) {
+  asm volatile(""
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :: "memory");
+}
+template <int N> __device__ __forceinline__ void tmem_wait_ld(uint32_t* a) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  reg_pin<N>(a);
+}
+template <int N> __device__ __forceinline__ void tmem_wait_ld(uint32_t* a, uint32_t* b) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  reg_pin<N>(a);
+  reg_pin<N>(b);
+}
+
 template <int N> __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* v);
 template <> __device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   __shared__ uint64_t xfull[kXStages], xempty[kXStages];
   __shared__ uint64_t opfull[Sh::kOpStages], opempty[Sh::kOpStages], bfull[Sh::kOpStages];
   __shared__ uint64_t accfull[kAccBufs], accempty[kAccBufs];
-  __shared__ uint64_t eafull[kEpiAlpha], eaempty[kEpiAlpha];
+  __shared__ uint64_t eafull[kEpiBufs], eaempty[kEpiBufs];
   __shared__ uint64_t drain;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort, s_np, s_nd, s_first, s_last;
@@ -350,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       mbar_init(smem_u32(&accfull[i]), 1);
       mbar_init(smem_u32(&accempty[i]), kEpi);
     }
-    for (int i = 0; i < kEpiAlpha; ++i) {
+    for (int i = 0; i < kEpiBufs; ++i) {
       mbar_init(smem_u32(&eafull[i]), 1);
       mbar_init(smem_u32(&eaempty[i]), kEpi);
     }
@@ -515,8 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 
   unsigned char* const xring = smem;
   unsigned char* const xalpha = smem + Sh::kXAlphaOff;
-  unsigned char* const ealpha = smem + Sh::kEAlphaOff;
-  float* const s_lm = reinterpret_cast<float*>(smem + Sh::kLmOff);
+  unsigned char* const epiring = smem + Sh::kEpiOff;
   unsigned char* const opring = smem + Sh::kOpOff;
   int issued_x = 0, issued_o = 0, issued_ea = 0, issued_mma = 0;   // for the drain after an abort
 
@@ -531,6 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         const float* alpha_src = a.plan + (size_t)p.tile * a.plan_stride + p.r0;
         const unsigned char* btab = a.btab + (size_t)(a.s_max - p.S) * Sh::kBBytes;
         const void* xmap = a.xmap;
+        const void* lmap = a.lmap;
         for (int ch = p.b; ch < p.e && ok; ++ch) {
           const int s = xi % kXStages;
           if (xi >= kXStages && !(ok = mbar_wait(smem_u32(&xempty[s]), ((xi / kXStages) - 1) & 1, spin, p.err, abort_flag))) break;
@@ -541,10 +566,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
           ++xi;
           issued_x = xi;
           if (first) {
-            const int ea = i % kEpiAlpha;
-            if (i >= kEpiAlpha && !(ok = mbar_wait(smem_u32(&eaempty[ea]), ((i / kEpiAlpha) - 1) & 1, spin, p.err, abort_flag))) break;
-            mbar_expect_tx(smem_u32(&eafull[ea]), kAlphaBytes);
-            bulk_load(smem_u32(ealpha + ea * kAlphaBytes), alpha_src, kAlphaBytes, smem_u32(&eafull[ea]));
+            // the epilogue's slot: alpha, and log a of the unit's outputs (rows r0.., outputs
+            // k0..; outside the image read as zeros, which the epilogue does not use)
+            const int eb = i % kEpiBufs;
+            if (i >= kEpiBufs && !(ok = mbar_wait(smem_u32(&eaempty[eb]), ((i / kEpiBufs) - 1) & 1, spin, p.err, abort_flag))) break;
+            unsigned char* const slot = epiring + eb * Sh::kEpiSlot;
+            const bool lm = MODE == 1 && a.lm_tma;
+            mbar_expect_tx(smem_u32(&eafull[eb]), kAlphaBytes + (lm ? Sh::kLmBytes : 0));
+            bulk_load(smem_u32(slot), alpha_src, kAlphaBytes, smem_u32(&eafull[eb]));
+            if (lm) tma_load_2d(smem_u32(slot + kAlphaBytes), lmap, p.r0, p.k0, smem_u32(&eafull[eb]));
             issued_ea = i + 1;
           }
           const int so = oi % Sh::kOpStages;
@@ -557,6 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         }
       }
     }
+    __syncwarp();                                         // reconverge before the CTA barriers
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue (one lane)
     if (lane == 0) {
@@ -601,11 +632,15 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     __syncwarp();
   } else if (warp < kProdWarps) {
     // ---------------------------------------------------------------- producers
-    const int ar = tid & (kTM - 1), aq = tid >> 7;
+    // thread (row ar, half ah) makes window positions 16 ah .. 16 ah + 15 of the stage, as two
+    // groups of 8 (one core-matrix row of A each)
+    const int ar = tid & (kTM - 1), ah = tid >> 7;
     // 128-byte swizzle of the x tile: 16-byte chunk j of row r sits at chunk j ^ (r % 8)
     const uint32_t xrow = (uint32_t)ar * 128u;
-    const uint32_t xc0 = (uint32_t)(((2 * aq) ^ (ar & 7)) * 16), xc1 = (uint32_t)(((2 * aq + 1) ^ (ar & 7)) * 16);
-    const uint32_t aoff = (uint32_t)((ar >> 3) * kGroupBytes + aq * 128 + (ar & 7) * 16);
+    uint32_t xc[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) xc[t] = xrow + (uint32_t)(((4 * ah + t) ^ (ar & 7)) * 16);
+    const uint32_t aoff = (uint32_t)((ar >> 3) * kGroupBytes + 2 * ah * 128 + (ar & 7) * 16);
     int xi = 0, oi = 0;
     bool ok = true;
     for (int i = 0; i < np && ok; ++i) {
@@ -618,31 +653,40 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         const int s = xi % kXStages;
         if (!(ok = mbar_wait(smem_u32(&xfull[s]), (xi / kXStages) & 1, spin, p.err, abort_flag))) break;
         if (ch == p.b && rowok) alpha = reinterpret_cast<const float*>(xalpha + s * kAlphaBytes)[ar];
-        const float4 x0 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc0);
-        const float4 x1 = *reinterpret_cast<const float4*>(xring + s * kXBytes + xrow + xc1);
-        mbar_arrive(smem_u32(&xempty[s]));
-        ++xi;
+        float4 xv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) xv[t] = *reinterpret_cast<const float4*>(xring + s * kXBytes + xc[t]);
         const int so = oi % Sh::kOpStages;
         if (oi >= Sh::kOpStages && !(ok = mbar_wait(smem_u32(&opempty[so]), ((oi / Sh::kOpStages) - 1) & 1, spin, p.err, abort_flag))) break;
         unsigned char* const stp = opring + so * Sh::kOpBytes;
-        float v[8];
-        const int m0 = p.lo + ch * kKC + aq * 8;         // absolute position of v[0]
-        if (alpha == -INFINITY) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) v[j] = 0.f;
-        } else {
-          // exponent e_j = x_j sc - (kc - m0 - j)^2 c - alpha = x_j sc + P + Q j - c j^2
-          const float dbase = (float)(p.kc - m0);
-          const float P = fmaf(-dbase * dbase, c, -alpha), Q = 2.f * dbase * c;
-          const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        for (int g = 0; g < 2; ++g) {
+          float v[8];
+          const int m0 = p.lo + ch * kKC + ah * 16 + g * 8;   // absolute position of v[0]
+          if (alpha == -INFINITY) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float K = fmaf(Q, (float)j, fmaf(-(float)(j * j), c, P));
-            v[j] = (m0 + j < len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
+            for (int j = 0; j < 8; ++j) v[j] = 0.f;
+          } else {
+            // exponent e_j = x_j sc - (kc - m0 - j)^2 c - alpha = x_j sc + P + Q j - c j^2
+            const float dbase = (float)(p.kc - m0);
+            const float P = fmaf(-dbase * dbase, c, -alpha), Q = 2.f * dbase * c;
+            const float4 a0 = xv[2 * g], a1 = xv[2 * g + 1];
+            const float xs[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float K = fmaf(Q, (float)j, fmaf(-(float)(j * j), c, P));
+              v[j] = (m0 + j < len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
+            }
           }
+          store_split8(v, stp + aoff + g * 128, stp + kABytes + aoff + g * 128);
         }
-        store_split8(v, stp + aoff, stp + kABytes + aoff);
+        // one proxy fence orders this thread's generic accesses of the stage against the async
+        // proxy: its A stores before the MMA reads them, and its reads of the x slot (and of
+        // alpha) before the next tensor copy into that slot overwrites them (without the
+        // fence the copy was seen to land before the reads)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&xempty[s]));
+        ++xi;
         mbar_arrive(smem_u32(&opfull[so]));
         ++oi;
       }
@@ -669,26 +713,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       const int k1 = min(p.k0 + TN, p.len) - 1;
       float* const y = a.y;
       float* const logsum = a.logsum;
-      const float* const lmarg = a.lmarg;
       int* const err = p.err;
       const float peps = p.eps;
-      // the potential-update pass: log a of this thread's outputs, into shared memory (each
-      // thread loads its own row; across the warp the loads of one output are contiguous)
-      if (MODE == 1 && rowok) {
-        for (int n = hcol; n < hcol + HN; ++n) {
-          const int k = min(p.k0 + n, k1);
-          const uint32_t dst = smem_u32(s_lm + n * kTM + rl);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(lmarg + (size_t)k * n_rows + row) : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-      }
-      const int ea = i % kEpiAlpha;
-      ok = mbar_wait(smem_u32(&eafull[ea]), (i / kEpiAlpha) & 1, spin, err, abort_flag);
+      // this piece's slot: alpha, then (potential update) log a as [TN][128]
+      const int eb = i % kEpiBufs;
+      const unsigned char* const eslot = epiring + eb * Sh::kEpiSlot;
+      const float* const s_lm = reinterpret_cast<const float*>(eslot + kAlphaBytes);
+      const bool lm_tma = a.lm_tma;      // else (rows not 16-byte aligned) log a from global
+      const float* const lmarg = a.lmarg;
+      ok = mbar_wait(smem_u32(&eafull[eb]), (i / kEpiBufs) & 1, spin, err, abort_flag);
       float alpha = -INFINITY;
-      if (ok) {
-        if (rowok) alpha = reinterpret_cast<const float*>(ealpha + ea * kAlphaBytes)[rl];
-        mbar_arrive(smem_u32(&eaempty[ea]));
-      }
+      if (ok && rowok) alpha = reinterpret_cast<const float*>(eslot)[rl];
       if (!epi_all(ok)) break;                            // the same for all epilogue threads
       if (lead) atomicAdd(a.tc_terms, (unsigned long long)(p.e - p.b) * kKC * TN * kTM);
       const float c = p.c;
@@ -696,14 +731,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       // the tilt of output column n: alpha + 2 (n - TN/2) (mref - kc) c
       const float tilt0 = fmaf(2.f * (float)(-TN / 2) * (mref - (float)p.kc), c, alpha);
       const float tstep = 2.f * (mref - (float)p.kc) * c;
-      bool lm_ready = false;
       // outputs (o = k0 + c0 + u, r = row) from CH sums
       auto emit = [&](int c0, const float* cv) {
         if (!rowok) return;
-        if (MODE == 1 && !lm_ready) {
-          asm volatile("cp.async.wait_all;" ::: "memory");
-          lm_ready = true;
-        }
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
           const int n = c0 + u;
@@ -721,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             y[yi] = out;
           } else {
             const float sv = __fmul_rn(out, kLn2);
-            const float lm = s_lm[n * kTM + rl];
+            const float lm = lm_tma ? s_lm[n * kTM + rl] : __ldg(lmarg + yi);
             float pot;
             if (lm == -INFINITY) {
               pot = -INFINITY;
@@ -752,7 +782,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
           uint32_t d1[CH], d2[CH];
           tmem_ld<CH>(tacc + (uint32_t)c0, d1);
           tmem_ld<CH>(tacc + (uint32_t)(TN + c0), d2);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          tmem_wait_ld<CH>(d1, d2);
           float cv[CH];
 #pragma unroll
           for (int u = 0; u < CH; ++u) cv[u] = __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
@@ -764,7 +794,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             if (j > 0) {                                  // running sum of chunks 0 .. j-1
               uint32_t f[CH];
               tmem_ld<CH>(tfold + (uint32_t)c0, f);
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+              tmem_wait_ld<CH>(f);
 #pragma unroll
               for (int u = 0; u < CH; ++u) cv[u] = __uint_as_float(f[u]) + cv[u];
             }
@@ -801,21 +831,34 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
 #pragma unroll
           for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
             float cv[CH];
-            for (int j = 0; j < p.nc; ++j) {
-              const float* sl = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN + c0;
+            const float* sl0 = tab.slots + (((size_t)p.ca * tab.slot_chunks) * kTM + rl) * TN + c0;
+            const size_t jstride = (size_t)kTM * TN;
+            for (int j0 = 0; j0 < p.nc; j0 += 2) {
+              // two chunks' loads in flight, then added in chunk order
+              float4 t4[2][CH / 4];
 #pragma unroll
-              for (int u = 0; u < CH; u += 4) {
-                const float4 t4 = __ldcg(reinterpret_cast<const float4*>(sl + u));
-                if (j == 0) {
-                  cv[u] = t4.x;
-                  cv[u + 1] = t4.y;
-                  cv[u + 2] = t4.z;
-                  cv[u + 3] = t4.w;
-                } else {
-                  cv[u] += t4.x;
-                  cv[u + 1] += t4.y;
-                  cv[u + 2] += t4.z;
-                  cv[u + 3] += t4.w;
+              for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+                for (int u = 0; u < CH; u += 4)
+                  t4[jj][u / 4] = (j0 + jj < p.nc) ? __ldcg(reinterpret_cast<const float4*>(sl0 + (j0 + jj) * jstride + u))
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int jj = 0; jj < 2; ++jj) {
+                if (j0 + jj >= p.nc) break;
+#pragma unroll
+                for (int u = 0; u < CH; u += 4) {
+                  const float4 q = t4[jj][u / 4];
+                  if (j0 + jj == 0) {
+                    cv[u] = q.x;
+                    cv[u + 1] = q.y;
+                    cv[u + 2] = q.z;
+                    cv[u + 3] = q.w;
+                  } else {
+                    cv[u] += q.x;
+                    cv[u + 1] += q.y;
+                    cv[u + 2] += q.z;
+                    cv[u + 3] += q.w;
+                  }
                 }
               }
             }
@@ -824,8 +867,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
           if (lead) a.ucnt[p.lu] = 0;
         }
       }
-      // the log-marginal prefetch lands before the next piece reuses its buffer
-      if (MODE == 1 && rowok) asm volatile("cp.async.wait_all;" ::: "memory");
+      // the slot is free once every epilogue thread is done with this piece's alpha and log a
+      // (reads ordered before the next copies into the slot by a proxy fence)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&eaempty[eb]));
     }
   }
 
@@ -854,15 +899,13 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         mbar_drain(smem_u32(&xfull[s]), ((issued_x - 1 - s) / kXStages) & 1);
       for (int s = 0; s < Sh::kOpStages && s < issued_o; ++s)
         mbar_drain(smem_u32(&bfull[s]), ((issued_o - 1 - s) / Sh::kOpStages) & 1);
-      for (int s = 0; s < kEpiAlpha && s < issued_ea; ++s)
-        mbar_drain(smem_u32(&eafull[s]), ((issued_ea - 1 - s) / kEpiAlpha) & 1);
+      for (int s = 0; s < kEpiBufs && s < issued_ea; ++s)
+        mbar_drain(smem_u32(&eafull[s]), ((issued_ea - 1 - s) / kEpiBufs) & 1);
     }
     if (warp == kMmaWarp && lane == 0 && issued_mma) {
       mma_commit(smem_u32(&drain));
       mbar_drain(smem_u32(&drain), 0);
     }
-    if (warp >= kEpiWarp0 && MODE == 1)
-      asm volatile("cp.async.wait_all;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -930,6 +973,22 @@ bool encode_xmap(BandArgs& a) {
   static_assert(sizeof(CUtensorMap) == sizeof(a.xmap), "tensor map size");
   return fn(reinterpret_cast<CUtensorMap*>(a.xmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims,
             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the log-marginal tensor map of a potential-update pass: lmarg as [len][n_rows] FP32 (the
+// layout of y), boxes of 128 rows x tn outputs, no swizzle; outside the image reads as zeros
+bool encode_lmap(BandArgs& a, int tn) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if ((a.n_rows & 3) != 0 || (reinterpret_cast<uintptr_t>(a.lmarg) & 15u) != 0) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)a.n_rows, (cuuint64_t)a.len};
+  cuuint64_t strides[1] = {(cuuint64_t)a.n_rows * 4};
+  cuuint32_t box[2] = {(cuuint32_t)kTM, (cuuint32_t)tn};
+  cuuint32_t estr[2] = {1, 1};
+  static_assert(sizeof(CUtensorMap) == sizeof(a.lmap), "tensor map size");
+  return fn(reinterpret_cast<CUtensorMap*>(a.lmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.lmarg),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1100,6 +1159,7 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx) {
     BandArgs a = t.p[q];
     a.tile_w = tw == 0 ? kBT : tw;
     if (tw != 0 && encode_xmap(a)) {
+      a.lm_tma = MODE == 1 && encode_lmap(a, tw);
       tctx[tt->n] = ctx[q];
       tt->p[tt->n++] = a;
     } else {
