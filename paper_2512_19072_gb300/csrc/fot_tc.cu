@@ -731,38 +731,55 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
       // the tilt of output column n: alpha + 2 (n - TN/2) (mref - kc) c
       const float tilt0 = fmaf(2.f * (float)(-TN / 2) * (mref - (float)p.kc), c, alpha);
       const float tstep = 2.f * (mref - (float)p.kc) * c;
-      // outputs (o = k0 + c0 + u, r = row) from CH sums
+      // outputs (o = k0 + c0 + u, r = row) from CH sums: all log2 first, then (potential
+      // update) all loads of log a, then the stores; one error check per call
+      const int nvalid = k1 - p.k0 + 1;                   // outputs of this tile inside the image
       auto emit = [&](int c0, const float* cv) {
         if (!rowok) return;
+        float out[CH];
+        bool bad = false;
 #pragma unroll
         for (int u = 0; u < CH; ++u) {
-          const int n = c0 + u;
-          const int k = p.k0 + n;
-          if (k > k1) break;
-          float out = -INFINITY;
-          if (alpha != -INFINITY) {
-            if (cv[u] > 0.f && cv[u] <= 3.4e38f)
-              out = __fadd_rn(fmaf((float)n, tstep, tilt0), lg2(cv[u]));
-            else
-              raise_error(err, FOT_ENONFINITE);
-          }
-          const size_t yi = (size_t)k * n_rows + row;
-          if (MODE == 0) {
-            y[yi] = out;
+          const bool okv = cv[u] > 0.f && cv[u] <= 3.4e38f;
+          out[u] = okv ? __fadd_rn(fmaf((float)(c0 + u), tstep, tilt0), lg2(cv[u])) : -INFINITY;
+          bad |= alpha != -INFINITY && !okv;
+        }
+        if (alpha == -INFINITY) {
+#pragma unroll
+          for (int u = 0; u < CH; ++u) out[u] = -INFINITY;
+        }
+        float* const yp = y + (size_t)(p.k0 + c0) * n_rows + row;
+        if (MODE == 0) {
+#pragma unroll
+          for (int u = 0; u < CH; ++u)
+            if (c0 + u < nvalid) yp[(size_t)u * n_rows] = out[u];
+        } else {
+          float lm[CH];
+          if (lm_tma) {
+#pragma unroll
+            for (int u = 0; u < CH; ++u) lm[u] = s_lm[(c0 + u) * kTM + rl];
           } else {
-            const float sv = __fmul_rn(out, kLn2);
-            const float lm = lm_tma ? s_lm[n * kTM + rl] : __ldg(lmarg + yi);
-            float pot;
-            if (lm == -INFINITY) {
-              pot = -INFINITY;
-            } else {
-              pot = __fmul_rn(peps, __fsub_rn(lm, sv));
-              if (!isfinite(pot)) raise_error(err, FOT_ENONFINITE);
-            }
-            y[yi] = pot;
-            if (logsum) logsum[yi] = sv;
+#pragma unroll
+            for (int u = 0; u < CH; ++u) lm[u] = c0 + u < nvalid ? __ldg(lmarg + (size_t)(p.k0 + c0 + u) * n_rows + row) : 0.f;
+          }
+          float pot[CH], sv[CH];
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            sv[u] = __fmul_rn(out[u], kLn2);
+            pot[u] = lm[u] == -INFINITY ? -INFINITY : __fmul_rn(peps, __fsub_rn(lm[u], sv[u]));
+            bad |= lm[u] != -INFINITY && !isfinite(pot[u]) && c0 + u < nvalid;
+          }
+#pragma unroll
+          for (int u = 0; u < CH; ++u)
+            if (c0 + u < nvalid) yp[(size_t)u * n_rows] = pot[u];
+          if (logsum) {
+            float* const lp = logsum + (size_t)(p.k0 + c0) * n_rows + row;
+#pragma unroll
+            for (int u = 0; u < CH; ++u)
+              if (c0 + u < nvalid) lp[(size_t)u * n_rows] = sv[u];
           }
         }
+        if (bad) raise_error(err, FOT_ENONFINITE);
       };
       for (int j = p.jlo; j < p.jhi; ++j) {
         const int ab = ai % kAccBufs;
