@@ -43,6 +43,9 @@ def _args():
     p.add_argument("--n", type=int, default=1024)
     p.add_argument("--iters", type=int, default=200)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sub", action="store_true",
+                   help="skip the sub-records of the single workload (2048^2, the 64-problem batch, "
+                        "iterations and time to a 1e-4 marginal violation)")
     p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity", "cfot"],
                    help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
                         "against looping single solves of the same problems; stopping: the "
@@ -117,9 +120,24 @@ def _oracle_sample(w, rows, budget_s):
     per_row = el / (reps * rows)
     t_iter = per_row * 4 * n
     return {"value": n * n / t_iter / 1e6, "unit": "Mpixel*iter/s", "cores": torch.get_num_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "extrapolated": True,
             "sample": f"{reps} x FP64 oracle axis pass over {rows} of {n} rows at n={n} "
                       f"(eps={eps:.4g} px^2); one iteration = 4 n row-passes, scaled"}
+
+
+def _oracle_full_256(iters):
+    """The oracle's whole Algorithm-1 iteration (fot_iterate, FP64) on the 256^2 downsample of
+    the single workload, for `iters` iterations: a measured rate, no extrapolation."""
+    import torch
+    from oracle import fot
+    w = _workload(256, iters)
+    g = np.asarray(w.g, dtype=np.float32).astype(np.float64)
+    G = np.asarray(w.G, dtype=np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    fot.fot_iterate(g, G, w.eps, iters)
+    el = time.perf_counter() - t0
+    return {"workload": w.name, "iters": iters, "seconds": el, "cores": torch.get_num_threads(),
+            "value": 256 * 256 * iters / el / 1e6, "unit": "Mpixel*iter/s"}
 
 
 def run_reference(a):
@@ -140,6 +158,9 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(w, a.n, a, ws),
             "cpu_baseline": s,
+            "extrapolated": "value: the oracle's FP64 axis pass timed on 16 rows of the 1024^2 "
+                            "workload's first iterate and scaled to 4 n row-passes per iteration",
+            "oracle_full_solve_256": _oracle_full_256(10),
             "e2e": {"value": v, "unit": "Mpixel*iter/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -285,6 +306,103 @@ def _roofline(n, a, ktimes, work, loop_ms):
     return roof
 
 
+def _timed_steps(step, steps, warmup, flush, stream):
+    """Median device time (ms) of `steps` calls of step() after `warmup` untimed ones, with an L2
+    flush (a 256 MB write) before every call, outside the events."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def _sub_single(B, n, prec_name, iters, steps, warmup, flush, stream):
+    """The single workload (config 3) at n^2 in one precision: fot_solve + fot_phase per step."""
+    import torch
+    w = _workload(n, iters)
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    prec = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED}[prec_name]
+    ctx = B.fot_create(n, n, prec)
+    phi, Dx, Dy = ctx.empty(), ctx.empty(), ctx.empty()
+
+    def step():
+        B.fot_solve(ctx, g, G, w.eps, iters)
+        B._check(B._lib.fot_phase(ctx._h, B._ptr(phi), B._ptr(Dx), B._ptr(Dy)), "fot_phase")
+
+    ms = _timed_steps(step, steps, warmup, flush, stream)
+    l1, _ = B.fot_marginal_error(ctx)
+    ctx.close()
+    return {"workload": w.name, "precision": prec_name, "value": n * n * iters / (ms * 1e-3) / 1e6,
+            "unit": "Mpixel*iter/s", "ms_per_step": ms, "steps": steps, "marginal_l1": l1}
+
+
+def _measure_batched(B, prec_name, iters, steps, warmup, stream, with_loop):
+    """Config 5 (64 problems of 128^2 .. 512^2) in one precision: one fot_batch_solve per step,
+    optionally against a loop of single solves of the same problems."""
+    import torch
+    from paper_2512_19072_gb300 import inputs
+    ws = inputs.config5(iters=iters)
+    prec = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED}[prec_name]
+    gs = [torch.from_numpy(w.g.astype(np.float32)).cuda() for w in ws]
+    Gs = [torch.from_numpy(w.G.astype(np.float32)).cuda() for w in ws]
+    eps = np.stack([w.eps for w in ws])
+    pix_iters = sum(w.g.size for w in ws) * iters
+    batch = B.fot_batch_create([w.g.shape for w in ws], prec)
+    flush = torch.empty(1, device="cuda")            # the batch's working set is below L2: no flush
+    ms_b = _timed_steps(lambda: B.fot_batch_solve(batch, gs, Gs, eps, iters), steps, warmup, flush, stream)
+    kernels, tensor = B.fot_batch_info(batch)
+    l1 = [B.fot_marginal_error(B.fot_batch_context(batch, q))[0] for q in range(len(ws))]
+    out = {"workload": "c5_64_problems_128_to_512", "precision": prec_name, "tensor_path": tensor,
+           "value": pix_iters / (ms_b * 1e-3) / 1e6, "unit": "Mpixel*iter/s", "ms_per_step": ms_b,
+           "steps": steps, "kernels_per_graph": kernels, "marginal_l1_max": max(l1),
+           "marginal_l1_mean": float(np.mean(l1)), "sizes": sorted(int(w.g.shape[0]) for w in ws)}
+    if with_loop:
+        ctxs = [B.fot_create(*w.g.shape, prec) for w in ws]
+
+        def loop():
+            for c, g, G, w in zip(ctxs, gs, Gs, ws):
+                B.fot_solve(c, g, G, w.eps, iters)
+
+        ms_l = _timed_steps(loop, max(1, steps // 2), 1, flush, stream)
+        out["loop_of_single_solves"] = {"value": pix_iters / (ms_l * 1e-3) / 1e6, "ms": ms_l}
+        out["speedup_vs_loop"] = ms_l / ms_b
+        for c in ctxs:
+            c.close()
+    batch.close()
+    return out
+
+
+def _sub_to_tol(B, n, prec_name, tol, max_iters, check_every, flush, stream):
+    """Iterations and device time of fot_solve_tol on the single workload until the marginal
+    violation sum |Gamma 1 - a| <= tol (Sec. 3), or max_iters."""
+    import torch
+    w = _workload(n, 1)
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    prec = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED}[prec_name]
+    ctx = B.fot_create(n, n, prec)
+    done = [0, 0.0]
+
+    def step():
+        done[0], done[1] = B.fot_solve_tol(ctx, g, G, w.eps[:1], max_iters, tol, check_every)
+
+    ms = _timed_steps(step, 1, 1, flush, stream)
+    ctx.close()
+    return {"precision": prec_name, "tol": tol, "reached": bool(done[1] <= tol), "iters": done[0],
+            "violation": done[1], "ms": ms, "max_iters": max_iters, "check_every": check_every}
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -410,6 +528,15 @@ def run_gpu(a):
                        "marginal_l1": l1_32, "marginal_l1_diff": abs(l1 - l1_32),
                        "mixed_speedup": value / v32}
             c32.close()
+        sub = None
+        if not a.no_sub and ws == 1 and n == 1024:
+            sub = {"note": "the same library on other workloads, each timed as the main line "
+                           "(L2 flush between steps, CUDA events); not part of value"}
+            sub["c3_2048"] = [_sub_single(B, 2048, p_, a.iters, 3, 2, flush, stream) for p_ in ("mixed", "fp32")]
+            sub["c5_batched"] = [_measure_batched(B, p_, 200, 3, 1, stream, with_loop=(p_ == "mixed"))
+                                 for p_ in ("mixed", "fp32")]
+            sub["c3_1024_to_violation_1e-4"] = [_sub_to_tol(B, n, p_, 1e-4, 4000, 100, flush, stream)
+                                                 for p_ in ("mixed", "fp32")]
         line = {"metric": METRIC if n == 1024 else METRIC.replace("1024^2", f"{n}^2"), "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -420,7 +547,7 @@ def run_gpu(a):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_v, "unit": "Mpixel*iter/s",
                         "h2d_bytes_per_step": 2 * n * n * 4, "d2h_bytes_per_step": n * n * 4},
-                "gpu_launches": launches, "clocks": clk, "fp32_form": compare,
+                "gpu_launches": launches, "clocks": clk, "fp32_form": compare, "sub_records": sub,
                 "paper_context": "1024^2, 200 iterations: 76 s Core i7 (2.76 Mpixel*iter/s), "
                                  "8.5 s T4 (24.7 Mpixel*iter/s)"}
         print(json.dumps(line), flush=True)

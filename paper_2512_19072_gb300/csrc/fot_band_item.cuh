@@ -50,10 +50,12 @@ constexpr int kSA = 8 * 36 + 4;   // floats per half-warp A block (8 rows x 36, 
 // The work of one (16-row group from row r0, 16 outputs from k0) item; PATH 0 = tilted GEMM,
 // PATH 1 = exact window sums.  Returns at once when the item belongs to the other PATH.
 // The plan entry is (row, pt): with a 16-wide plan pt = k0 / 16; a wider plan tile holding
-// these outputs gives a window that covers theirs, and then only PATH 1 may be used
-// (EXACT_ONLY), since its alpha is not the maximum at this item's centre.
+// these outputs gives a window that covers theirs, and then its alpha is not the maximum at
+// this item's centre: either only PATH 1 may be used (EXACT_ONLY), or the item first takes
+// every row's exact maximum over its window at its own centre (OWN_ALPHA, one sweep of the
+// window without exponentials) and then both paths apply.
 // sAw: this warp's 2 * kSA floats of shared memory.
-template <int MODE, int PATH, bool EXACT_ONLY = false>
+template <int MODE, int PATH, bool EXACT_ONLY = false, bool OWN_ALPHA = false>
 __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int k0, float* sAw) {
   const int lane = threadIdx.x & 31;
   const int h = lane >> 4, i = lane & 15;
@@ -85,6 +87,25 @@ __device__ __forceinline__ void band_item(const BandArgs& a, int r0, int pt, int
     W = max(W, wl[rr]);
   }
   W = max(W, __shfl_xor_sync(0xffffffffu, W, 16));        // common to both halves
+  if (OWN_ALPHA) {
+    // alpha_r = max over the row's window of x_r[m] sc - (kc - m)^2 c (the exponent PATH 0
+    // forms), lanes of a half-warp striding the window, then a max over the half-warp
+#pragma unroll
+    for (int rr = 0; rr < kBR; ++rr) {
+      float mx = -INFINITY;
+      if (alpha[rr] != -INFINITY) {
+        const float* xr = a.x + (size_t)(rh + rr) * a.len;
+        for (int mp = i; mp < wl[rr]; mp += kBT) {
+          const int m = lo[rr] + mp;
+          const float d = (float)(kc - m);
+          mx = fmaxf(mx, fmaf(-d * d, c, xr[m] * sc));
+        }
+      }
+#pragma unroll
+      for (int o = kBT / 2; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (alpha[rr] != -INFINITY) alpha[rr] = mx;
+    }
+  }
   const int k = k0 + i;
   const float kap = (float)(k - kc);
   const float kmax = (float)(kBT / 2);

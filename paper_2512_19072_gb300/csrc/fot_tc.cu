@@ -80,7 +80,7 @@ constexpr int kGroupBytes = (kKC / 8) * 128;   // 512 B between 8-row core-matri
 constexpr float kTiltMaxTC = 48.f;
 constexpr int kMaxPieces = 128;          // units one CTA's share may touch
 constexpr int kChunk = 4;                // stages per accumulation chunk
-constexpr int kMaxDecl = 64;             // CUDA-core units per CTA
+constexpr int kMaxDecl = 128;            // CUDA-core items (16 rows x 16 outputs) per CTA
 constexpr int kUnitsPerThread = 8;       // units each thread holds during the set-up scan
 constexpr int kSpinDefault = 1 << 20;    // bounded mbarrier polls
 constexpr int kRouteKC = 64;             // window rounding of the host's tile-width estimate
@@ -236,6 +236,10 @@ __device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p
 
 // tensor-memory load / store of N consecutive 32-bit columns of this warp's 32 lanes
 template <int N> __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
+template <> __device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr));
+}
 template <> __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
@@ -252,6 +256,9 @@ template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t
 // registers pass through the wait as read-write operands, so no use of them can be scheduled
 // before the wait (a "memory" clobber orders memory accesses only, not register arithmetic).
 template <int N> __device__ __forceinline__ void reg_pin(uint32_t* v);
+template <> __device__ __forceinline__ void reg_pin<4>(uint32_t* v) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]) :: "memory");
+}
 template <> __device__ __forceinline__ void reg_pin<8>(uint32_t* v) {
   asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]) :: "memory");
 }
@@ -272,6 +279,10 @@ template <int N> __device__ __forceinline__ void tmem_wait_ld(uint32_t* a, uint3
 }
 
 template <int N> __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* v);
+template <> __device__ __forceinline__ void tmem_st<4>(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+               :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+}
 template <> __device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
@@ -287,10 +298,11 @@ template <> __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const ui
 
 // the CTA holding stage x of the pass when S stages are shared out over C CTAs (CTA k takes
 // [k S / C, (k + 1) S / C))
-__device__ __forceinline__ int cta_of(long long x, long long S, int C) {
-  return (int)(((x + 1) * C - 1) / S);
+// (32-bit arithmetic: the host keeps S * C below 2^32)
+__device__ __forceinline__ int cta_of(uint32_t x, uint32_t S, uint32_t C) {
+  return (int)(((x + 1u) * C - 1u) / S);
 }
-__device__ __forceinline__ long long share_start(int k, long long S, int C) { return (long long)k * S / C; }
+__device__ __forceinline__ uint32_t share_start(uint32_t k, uint32_t S, uint32_t C) { return k * S / C; }
 
 // what a unit needs: its stage count when it takes the tensor cores (0 otherwise), whether it
 // takes the CUDA-core sums instead, its union window start.  Every CTA must derive the same
@@ -309,20 +321,22 @@ __device__ __forceinline__ void unit_info(const BandTable<MAXP>& tab, int u, int
   decl = take ? 0 : 1;
 }
 
-// CUDA-core window sums of a unit outside the tensor path: 16-row items, the tile's 16-wide
-// parts (for a wider tile the exact window sums over the tile's window)
+// CUDA-core window sums of one 16-row x 16-output item of a unit outside the tensor path
+// (item it: rows r0 + 16 (it % 8), outputs k0 + 16 (it / 8)).  For a wider tile the item first
+// takes its rows' maxima at its own centre, then the tilted GEMM or, where the item's own tilt
+// bound fails too, the exact window sums.
+constexpr int kRowItems = kTM / (2 * kBR);               // 8 row groups of 16 per unit
 template <int MODE, int TN>
-__device__ __noinline__ void tc_cuda_core_unit(const BandArgs& a, int r0, int tile, int k0, int warp, float* sAw) {
-  for (int it = warp; it < (kTM / (2 * kBR)) * (TN / kBT); it += kProdWarps) {
-    const int rw = r0 + (it % (kTM / (2 * kBR))) * 2 * kBR;
-    const int kq = k0 + (it / (kTM / (2 * kBR))) * kBT;
-    if (rw >= a.n_rows || kq >= a.len) continue;           // warp-uniform
-    if (TN == kBT) {
-      band_item<MODE, 0>(a, rw, tile, kq, sAw);
-      band_item<MODE, 1>(a, rw, tile, kq, sAw);
-    } else {
-      band_item<MODE, 1, true>(a, rw, tile, kq, sAw);
-    }
+__device__ __noinline__ void tc_cuda_core_item(const BandArgs& a, int r0, int tile, int k0, int it, float* sAw) {
+  const int rw = r0 + (it % kRowItems) * 2 * kBR;
+  const int kq = k0 + (it / kRowItems) * kBT;
+  if (rw >= a.n_rows || kq >= a.len) return;             // warp-uniform
+  if (TN == kBT) {
+    band_item<MODE, 0>(a, rw, tile, kq, sAw);
+    band_item<MODE, 1>(a, rw, tile, kq, sAw);
+  } else {
+    band_item<MODE, 0, false, true>(a, rw, tile, kq, sAw);
+    band_item<MODE, 1, false, true>(a, rw, tile, kq, sAw);
   }
 }
 
@@ -330,8 +344,9 @@ template <int MODE, int TN, int MAXP>
 __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_constant__ BandTable<MAXP> tab) {
   using Sh = TcShape<TN>;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned base (the 128-byte swizzle of the x tiles), formed by pointer arithmetic
+  // on the shared array so that every access through it compiles as a shared-memory access
+  unsigned char* const smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t xfull[kXStages], xempty[kXStages];
   __shared__ uint64_t opfull[Sh::kOpStages], opempty[Sh::kOpStages], bfull[Sh::kOpStages];
   __shared__ uint64_t accfull[kAccBufs], accempty[kAccBufs];
@@ -425,14 +440,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     tot_s += s_wsum[w][0];
     tot_t += s_wsum[w][1];
   }
-  const long long S_tot = tot_s;
-  const long long sb = S_tot > 0 ? share_start(cta, S_tot, C) : 0;
-  const long long se = S_tot > 0 ? share_start(cta + 1, S_tot, C) : 0;
+  const uint32_t S_tot = (uint32_t)tot_s;
+  const uint32_t sb = S_tot > 0 ? share_start(cta, S_tot, C) : 0u;
+  const uint32_t se = S_tot > 0 ? share_start(cta + 1, S_tot, C) : 0u;
   // this CTA takes the chunks of unit u that start in [sb, se): chunks [jlo, jhi)
-  auto chunks_here = [&](long long P, int S, int& jlo, int& jhi) {
+  auto chunks_here = [&](uint32_t P, int S, int& jlo, int& jhi) {
     const int nc = (S + kChunk - 1) / kChunk;
-    jlo = sb > P ? (int)min((long long)nc, (sb - P + kChunk - 1) / kChunk) : 0;
-    jhi = se > P ? (int)min((long long)nc, (se - P + kChunk - 1) / kChunk) : 0;
+    jlo = sb > P ? min(nc, (int)((sb - P + kChunk - 1) / kChunk)) : 0;
+    jhi = se > P ? min(nc, (int)((se - P + kChunk - 1) / kChunk)) : 0;
   };
   {
     long long P = base_s, R = base_t & 0xffffffffll;
@@ -464,26 +479,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
             const int nc = (uS[i] + kChunk - 1) / kChunk;
             int ncon = 0, prev = -1;
             for (int jj = 0; jj < nc; ++jj) {
-              const int k = cta_of(P + (long long)jj * kChunk, S_tot, C);
+              const int k = cta_of((uint32_t)P + (uint32_t)(jj * kChunk), S_tot, C);
               if (k != prev) {
                 ++ncon;
                 prev = k;
               }
             }
-            s_pcon[idx] = make_int4(cta_of(P, S_tot, C), prev, ncon, 0);
+            s_pcon[idx] = make_int4(cta_of((uint32_t)P, S_tot, C), prev, ncon, 0);
             atomicMax(&s_np, idx + 1);
           } else {
             raise_error(err0, FOT_EUNSUPPORTED);
           }
         }
       }
-      if (uD[i] && (int)(D % C) == cta) {
-        const int idx = (int)(D / C);
-        if (idx < kMaxDecl) {
-          s_decl[idx] = u0 + i;
-          atomicMax(&s_nd, idx + 1);
-        } else {
-          raise_error(err0, FOT_EUNSUPPORTED);
+      if (uD[i]) {
+        // the declined unit's items q = D * IPU + it are dealt round-robin over the CTAs
+        constexpr int IPU = kRowItems * (TN / kBT);
+        const long long q0 = D * IPU;
+        for (int it = (int)((cta - q0 % C + C) % C); it < IPU; it += C) {
+          const int idx = atomicAdd(&s_nd, 1);
+          if (idx < kMaxDecl)
+            s_decl[idx] = ((u0 + i) << 8) | it;
+          else
+            raise_error(err0, FOT_EUNSUPPORTED);
         }
       }
       P += uS[i];
@@ -695,7 +713,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
     // ---------------------------------------------------------------- epilogue
     // two warps per tensor-memory lane quarter (warp % 4), each taking half of the columns
     constexpr int HN = TN / 2;                            // columns of this thread
-    constexpr int CH = HN < 16 ? HN : 16;                 // columns per tensor-memory load
+    // columns per step: the column loops are not unrolled, so that the epilogue's code stays
+    // small (it runs once per unit, between long stretches of producer code, and a large
+    // unrolled body was fetched cold every time)
+    constexpr int CH = 4;
     const int q4 = warp & 3;
     const int hcol = ((warp - kEpiWarp0) >> 2) * HN;      // first column of this thread's half
     const int rl = 32 * q4 + lane;                        // accumulator row
@@ -794,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         // chunk sum = D[0:TN) + D[TN:2TN) (the three split products), CH columns at a time; a
         // split unit's chunk sums go to its slots, the others are added to the running sum
         float* slot = tab.slots + (((size_t)p.ca * tab.slot_chunks + j) * kTM + rl) * TN;
-#pragma unroll
+#pragma unroll 1
         for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
           uint32_t d1[CH], d2[CH];
           tmem_ld<CH>(tacc + (uint32_t)c0, d1);
@@ -845,11 +866,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         }
         asm volatile("bar.sync 1, %0;" :: "r"(kEpi) : "memory");
         if (s_last) {
-#pragma unroll
+#pragma unroll 1
           for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
             float cv[CH];
             const float* sl0 = tab.slots + (((size_t)p.ca * tab.slot_chunks) * kTM + rl) * TN + c0;
             const size_t jstride = (size_t)kTM * TN;
+#pragma unroll 1
             for (int j0 = 0; j0 < p.nc; j0 += 2) {
               // two chunks' loads in flight, then added in chunk order
               float4 t4[2][CH / 4];
@@ -898,12 +920,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   if (warp < kProdWarps) asm volatile("bar.sync 3, %0;" :: "r"(kProd) : "memory");
   if (warp < kProdWarps && !*abort_flag) {
     float* sAw = reinterpret_cast<float*>(xring) + warp * 2 * kSA;
-    for (int d = 0; d < nd; ++d) {
-      const int u = s_decl[d];
+    for (int d = warp; d < min(nd, kMaxDecl); d += kProdWarps) {
+      const int u = s_decl[d] >> 8, it = s_decl[d] & 255;
       const BandArgs& a = tab.p[find_prob<MAXP, 3>(tab, u)];
       const int lu = u - a.cta_base;
       const int tile = lu % a.n_tiles;
-      tc_cuda_core_unit<MODE, TN>(a, (lu / a.n_tiles) * kTM, tile, tile * TN, warp, sAw);
+      tc_cuda_core_item<MODE, TN>(a, (lu / a.n_tiles) * kTM, tile, tile * TN, it, sAw);
     }
   }
 
@@ -1195,8 +1217,12 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx) {
       if (o->slot_chunks > ts->slot_chunks) ts = o;
     }
     const int sms = ts->sms;
-    if (tt->ctas > kThreads * kUnitsPerThread || tt->ctas > (kMaxPieces / 2) * sms) {
-      // more units than the kernel's set-up holds: the CUDA-core sums for all of them
+    int smax_all = 1;
+    for (int q = 0; q < tt->n; ++q) smax_all = std::max(smax_all, tt->p[q].s_max);
+    if (tt->ctas > kThreads * kUnitsPerThread || tt->ctas > (kMaxPieces / 2) * sms ||
+        (uint64_t)tt->ctas * (uint64_t)smax_all * (uint64_t)sms >= (1ull << 32)) {
+      // more units than the kernel's set-up holds (or stage positions beyond its 32-bit
+      // partition arithmetic): the CUDA-core sums for all of them
       for (int q = 0; q < tt->n; ++q) {
         BandArgs a = tt->p[q];
         a.ext_lo = a.ext_hi = nullptr;

@@ -1,6 +1,9 @@
-"""Comparison helpers shared by the GPU parity tests (no method arithmetic here)."""
+"""Comparison helpers shared by the GPU parity tests (no method arithmetic here beyond the
+oracle calls that size an error bound)."""
 import numpy as np
 import torch
+
+from oracle import fot
 
 # FP32 tolerance for potentials, normwise relative over finite entries (the bound the
 # method's FP32 path is held to).
@@ -50,3 +53,33 @@ def normwise(gpu, ref):
     ref = np.asarray(ref, dtype=np.float64)
     fin = np.isfinite(ref)
     return np.abs(gpu[fin] - ref[fin]).max() / max(np.abs(ref[fin]).max(), 1e-30)
+
+
+def phase_step_bound(psi, S_last, eps, dx, phi_ref, rounding=8):
+    """A-priori bound on |phi_gpu - phi_ref| when both take the phase step (Eqs. 9-10, then
+    the trapezoid rule) from the same (psi, S_last) and the GPU works in FP32.
+
+    Every moment weight is exp of a log value of magnitude <= lmax (psi/eps, the Gaussian
+    exponent, S_last); `rounding` FP32 roundings of such values change it by a relative
+    d <= rounding * 2^-24 * lmax.  The first moments then move by at most (e^(2d) - 1) max|X| W,
+    W = sum of the weights = exp(S(psi) - S_last), and the trapezoid steps add these along
+    their path (the centre column, then the row), plus FP32 rounding of the running sums."""
+    n_r, n_c = psi.shape
+    fin_p = np.isfinite(psi)
+    S_psi = fot.log_kernel_apply(psi, eps)
+    fin_w = np.isfinite(S_psi) & np.isfinite(S_last)
+    W = np.where(fin_w, np.exp(np.where(fin_w, S_psi - S_last, 0.0)), 0.0)
+    lmax = np.abs(S_last[fin_w]).max() + np.abs(psi[fin_p]).max() / eps
+    d = rounding * 2.0 ** -24 * lmax
+    Xmax = max(n_r, n_c) // 2 / (max(n_r, n_c) * dx)
+    Bd = np.expm1(2 * d) * Xmax * W
+    cr, cc = n_r // 2, n_c // 2
+    seg_c = dx * 0.5 * (Bd[1:, cc] + Bd[:-1, cc])
+    col = np.zeros(n_r)
+    col[cr + 1:] = np.cumsum(seg_c[cr:])
+    col[:cr] = np.cumsum(seg_c[:cr][::-1])[::-1]
+    seg_r = dx * 0.5 * (Bd[:, 1:] + Bd[:, :-1])
+    row = np.zeros((n_r, n_c))
+    row[:, cc + 1:] = np.cumsum(seg_r[:, cc:], axis=1)
+    row[:, :cc] = np.cumsum(seg_r[:, :cc][:, ::-1], axis=1)[:, ::-1]
+    return col[:, None] + row + (n_r + n_c) * 2.0 ** -23 * np.abs(phi_ref).max(), Bd
