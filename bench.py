@@ -37,7 +37,7 @@ def _args():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="fot", choices=["fot", "reference"])
-    p.add_argument("--precision", default="mixed", choices=["fp32", "fp32_dense", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp32", "fp32_dense", "mixed", "bf16"])
     p.add_argument("--no-compare", action="store_true",
                    help="skip the FP32 comparison run of the mixed form")
     p.add_argument("--n", type=int, default=1024)
@@ -46,7 +46,7 @@ def _args():
     p.add_argument("--no-sub", action="store_true",
                    help="skip the sub-records of the single workload (2048^2, the 64-problem batch, "
                         "iterations and time to a 1e-4 marginal violation)")
-    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity", "cfot"],
+    p.add_argument("--workload", default="single", choices=["single", "batched", "stopping", "intensity", "cfot", "sweep"],
                    help="batched: the 64-problem uneven-size batch (one graph launch per solve) "
                         "against looping single solves of the same problems; stopping: the "
                         "single workload solved to a marginal-violation tolerance; intensity: the "
@@ -332,7 +332,7 @@ def _sub_single(B, n, prec_name, iters, steps, warmup, flush, stream):
     w = _workload(n, iters)
     g = torch.from_numpy(w.g.astype(np.float32)).cuda()
     G = torch.from_numpy(w.G.astype(np.float32)).cuda()
-    prec = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED}[prec_name]
+    prec = {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED, "bf16": B.FOT_BF16}[prec_name]
     ctx = B.fot_create(n, n, prec)
     phi, Dx, Dy = ctx.empty(), ctx.empty(), ctx.empty()
 
@@ -418,7 +418,8 @@ def run_gpu(a):
     g = torch.from_numpy(w.g.astype(np.float32)).cuda()
     G = torch.from_numpy(w.G.astype(np.float32)).cuda()
     eps = w.eps
-    prec = {"fp32": B.FOT_FP32, "fp32_dense": B.FOT_FP32_DENSE, "mixed": B.FOT_MIXED}[a.precision]
+    prec = {"fp32": B.FOT_FP32, "fp32_dense": B.FOT_FP32_DENSE, "mixed": B.FOT_MIXED,
+            "bf16": B.FOT_BF16}[a.precision]
     ctx = B.fot_create(n, n, prec)
     phi = ctx.empty()
     Dx = ctx.empty()
@@ -533,6 +534,8 @@ def run_gpu(a):
             sub = {"note": "the same library on other workloads, each timed as the main line "
                            "(L2 flush between steps, CUDA events); not part of value"}
             sub["c3_2048"] = [_sub_single(B, 2048, p_, a.iters, 3, 2, flush, stream) for p_ in ("mixed", "fp32")]
+            sub["c3_1024_single_bf16"] = _sub_single(B, 1024, "bf16", a.iters, 3, 2, flush, stream)
+            sub["c3_1024_single_bf16"]["error_bound"] = "2^-6 eps per half-step (split-BF16 mixed: 2^-15 eps)"
             sub["c5_batched"] = [_measure_batched(B, p_, 200, 3, 1, stream, with_loop=(p_ == "mixed"))
                                  for p_ in ("mixed", "fp32")]
             sub["c3_1024_to_violation_1e-4"] = [_sub_to_tol(B, n, p_, 1e-4, 4000, 100, flush, stream)
@@ -540,7 +543,7 @@ def run_gpu(a):
         line = {"metric": METRIC if n == 1024 else METRIC.replace("1024^2", f"{n}^2"), "value": value, "unit": "Mpixel*iter/s", "n_gpus": ws,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16+f32" if a.precision == "mixed" else "f32",
+                "dtype": {"mixed": "bf16+f32", "bf16": "bf16x1+f32"}.get(a.precision, "f32"),
                 "data": "synthetic (seeded two-Gaussian beam -> 12-shape composite target)",
                 "config": _config(w, n, a, ws),
                 "marginal_l1": l1, "dual_objective": dual,
@@ -731,6 +734,56 @@ def run_intensity(a):
     return 0
 
 
+def run_sweep(a):
+    """Fig. 3 of Sec. 5: the L1 intensity loss |F[g e^{2 pi i phi}]|^2 - G^2 of the phase after
+    T iterations, against eps (paper units), for FOT (this build's mixed form) and cFOT (FP32
+    exponential domain), on the two-Gaussian beam -> 12-shape target at n^2 (512 by default for
+    this workload).  One solve per (form, eps) continued with fot_resume between the iteration
+    counts (fixed eps, so the same iterates as separate solves); cFOT restarts for each count.
+    A cFOT run whose potentials leave the FP32 range is reported as unstable."""
+    import torch
+    from paper_2512_19072_gb300 import binding as B
+    n = a.n if a.n != 1024 else 512
+    w = _workload(n, 1)
+    g = torch.from_numpy(w.g.astype(np.float32)).cuda()
+    G = torch.from_numpy(w.G.astype(np.float32)).cuda()
+    eps_list = [5e-5, 1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2, 1e-1]
+    iter_list = [50, 100, 200, 400]
+    table = {"fot": {}, "cfot": {}}
+    ctx = B.fot_create(n, n, B.FOT_MIXED)
+    t0 = time.perf_counter()
+    for e in eps_list:
+        row, done = [], 0
+        for T in iter_list:
+            if done == 0:
+                B.fot_solve(ctx, g, G, [e], T, eps_units=B.FOT_EPS_PAPER)
+            else:
+                B.fot_resume(ctx, [e], T - done, eps_units=B.FOT_EPS_PAPER)
+            done = T
+            phi, _, _ = B.fot_phase(ctx)
+            row.append(B.fot_intensity_loss(ctx, phi))
+        table["fot"][f"{e:g}"] = row
+        crow = []
+        for T in iter_list:
+            try:
+                B.fot_cfot_solve(ctx, g, G, [e], T, eps_units=B.FOT_EPS_PAPER)
+                phi, _, _ = B.fot_phase(ctx)
+                crow.append(B.fot_intensity_loss(ctx, phi))
+            except B.FotError as err:
+                crow.append("unstable" if B.STATUS.get(err.status) == "FOT_ENONFINITE" else str(err))
+        table["cfot"][f"{e:g}"] = crow
+    el = time.perf_counter() - t0
+    ctx.close()
+    line = {"metric": "L1 intensity loss vs eps and iterations (Fig. 3)", "value": None, "unit": "L1",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "bf16+f32 (FOT), f32 (cFOT)",
+            "data": "synthetic (seeded two-Gaussian beam -> 12-shape composite target)",
+            "config": {"workload": w.name, "n": n, "eps_paper": eps_list, "iterations": iter_list,
+                       "eps_px2": [e * n * n for e in eps_list]},
+            "loss": table, "seconds": el}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_cfot(a):
     """cFOT (FFT convolutions, exponential domain, FP32) against FOT (banded passes, the
     context's mixed form) per iteration, on two beams over a flat floor at n^2 and a large
@@ -805,6 +858,8 @@ def main():
         return run_intensity(a)
     if a.workload == "cfot":
         return run_cfot(a)
+    if a.workload == "sweep":
+        return run_sweep(a)
     return run_gpu(a)
 
 

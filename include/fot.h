@@ -64,8 +64,13 @@ typedef enum {
                             FP32 accumulation in TMEM) with FP32 log-domain potentials */
   FOT_FP32_DENSE = 2,    /* FP32 on the CUDA cores, every output scans every term with its
                             own exact maximum (one exponential per term): the plain form */
-  FOT_AUTO = 3           /* batches only: time FOT_FP32 and FOT_MIXED on the batch when its
+  FOT_AUTO = 3,          /* batches only: time FOT_FP32 and FOT_MIXED on the batch when its
                             graph is built and keep the faster */
+  FOT_BF16 = 4           /* the tensor-core banded GEMM of FOT_MIXED with single BF16
+                            operands: one MMA per term instead of three; each product carries
+                            up to 2^-7 relative error (both operands rounded to 8 significant
+                            bits), so a half-step moves f or psi by at most 2^-6 eps (against
+                            2^-15 eps for FOT_MIXED); single contexts only */
 } fot_precision;
 
 typedef enum { FOT_EPS_PX2 = 0, FOT_EPS_PAPER = 1 } fot_eps_units;
@@ -119,6 +124,24 @@ fot_status fot_resume(fot_ctx* ctx, const double* eps, int n_eps, int eps_units,
 fot_status fot_solve_tol(fot_ctx* ctx, const float* g, const float* G, double dx,
                          const double* eps, int n_eps, int eps_units, int max_iters, double tol,
                          int check_every, int* iters_out, double* tv_out);
+
+/* Automatic eps (Sec. 5, the eps hyperparameter: as low as possible while the Sinkhorn
+ * iterations stay stable).  Tries the n_cand candidate values cand[] in increasing order; for
+ * each it runs, from the standard start, check_every iterations and then the rest of a probe of
+ * probe_iters iterations (fot_solve + fot_resume in this context's precision, or cFOT from the
+ * start for each part when use_cfot), measuring the marginal violation tv = sum |Gamma 1 - a|
+ * (as fot_solve_tol) after the first part (tv1) and at the end (tv2).  A candidate is stable when
+ * no potential became non-finite and tv2 <= (1 - min_decrease) tv1; the smallest stable one is
+ * chosen.  *index_out receives its index in cand[] (-1 when none is stable), *tv_out (may be
+ * NULL) its tv2; afterwards the context holds the last probe's iterate (the chosen candidate's
+ * when one was found).  eps_units and dx as in fot_solve.  Errors: FOT_EINVAL (null pointers,
+ * n_cand < 1, a candidate not finite and > 0, check_every < 1, probe_iters <= check_every,
+ * min_decrease outside [0, 1)); FOT_EUNSUPPORTED (use_cfot on a shape cFOT does not take);
+ * other errors of the solves are returned as they occur (a non-finite potential only rejects
+ * its candidate). */
+fot_status fot_select_eps(fot_ctx* ctx, const float* g, const float* G, double dx, const double* cand,
+                          int n_cand, int eps_units, int probe_iters, int check_every,
+                          double min_decrease, int use_cfot, int* index_out, double* tv_out);
 
 /* cFOT (Sec. 3.1): the same problem, start and eps rules as fot_solve, but the iterations run
  * Algorithm 1 in the exponential domain with every Lambda product replaced by a linear

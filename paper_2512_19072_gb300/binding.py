@@ -23,7 +23,7 @@ if not os.path.exists(LIB_PATH):
 
 _lib = ctypes.CDLL(LIB_PATH)
 
-FOT_FP32, FOT_MIXED, FOT_FP32_DENSE, FOT_AUTO = 0, 1, 2, 3
+FOT_FP32, FOT_MIXED, FOT_FP32_DENSE, FOT_AUTO, FOT_BF16 = 0, 1, 2, 3, 4
 FOT_EPS_PX2, FOT_EPS_PAPER = 0, 1
 FOT_KERNEL_PLAN, FOT_KERNEL_BAND, FOT_KERNEL_TENSOR, FOT_KERNEL_DENSE = 0, 1, 2, 3
 FOT_KERNEL_CLASSES = 4
@@ -45,6 +45,7 @@ _SIGS = {
     "fot_resume": (_I, [_P, _DP, _I, _I, _I]),
     "fot_cfot_solve": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I]),
     "fot_solve_tol": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
+    "fot_select_eps": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
     "fot_sync": (_I, [_P]),
     "fot_potentials": (_I, [_P, _P, _P]),
     "fot_set_potentials": (_I, [_P, _P, _P]),
@@ -174,6 +175,19 @@ def fot_solve_tol(ctx, g, G, eps, max_iters, tol, check_every, dx=0.0, eps_units
                               float(tol), int(check_every), ctypes.byref(it), ctypes.byref(tv)),
            "fot_solve_tol")
     return it.value, tv.value
+
+
+def fot_select_eps(ctx, g, G, candidates, probe_iters, check_every, min_decrease=0.1, use_cfot=False,
+                   dx=0.0, eps_units=FOT_EPS_PX2):
+    """Smallest stable eps among the candidates: returns (index into candidates or -1, tv)."""
+    c = np.ascontiguousarray(np.asarray(candidates, dtype=np.float64).ravel())
+    idx = ctypes.c_int(-1)
+    tv = ctypes.c_double(0.0)
+    ctx._sync_stream()
+    _check(_lib.fot_select_eps(ctx._h, _ptr(g), _ptr(G), float(dx), c.ctypes.data_as(_DP), len(c), eps_units,
+                               int(probe_iters), int(check_every), float(min_decrease), int(bool(use_cfot)),
+                               ctypes.byref(idx), ctypes.byref(tv)), "fot_select_eps")
+    return idx.value, tv.value
 
 
 def fot_resume(ctx, eps, iters=None, eps_units=FOT_EPS_PX2):

@@ -138,7 +138,8 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
   if (!out) return FOT_EINVAL;
   *out = nullptr;
   if (rows < 1 || cols < 1 || rows > kMaxDim || cols > kMaxDim) return FOT_EINVAL;
-  if (precision != FOT_FP32 && precision != FOT_MIXED && precision != FOT_FP32_DENSE)
+  if (precision != FOT_FP32 && precision != FOT_MIXED && precision != FOT_FP32_DENSE &&
+      precision != FOT_BF16)
     return FOT_EINVAL;
   if (getenv("FOT_FAULT_INJECT_ENOMEM")) return FOT_ENOMEM;   // host-side fault injection
   int ndev = 0;
@@ -175,7 +176,7 @@ fot_status fot_create(fot_ctx** out, int rows, int cols, int precision, int devi
     fot_destroy(c);
     return FOT_ECUDA;
   }
-  if (ok && precision == FOT_MIXED) {
+  if (ok && (precision == FOT_MIXED || precision == FOT_BF16)) {
     if (!tc_supported(rows, cols)) {
       fot_destroy(c);
       return FOT_EUNSUPPORTED;
@@ -310,7 +311,7 @@ fot_status fot_set_problem(fot_ctx* c, const float* g, const float* G) {
 
 static void half_step(fot_ctx* c, const float* pot_in, const float* lmarg, double eps,
                       float* pot_out, float* logsum) {
-  if (c->precision == FOT_MIXED && c->tc)
+  if ((c->precision == FOT_MIXED || c->precision == FOT_BF16) && c->tc)
     half_step_tc(c, pot_in, lmarg, eps, pot_out, logsum);
   else if (c->precision == FOT_FP32_DENSE)
     half_step_simt(c, pot_in, lmarg, eps, pot_out, logsum, c->R);
@@ -482,6 +483,57 @@ fot_status fot_solve_tol(fot_ctx* c, const float* g, const float* G, double dx, 
   }
   *iters_out = done;
   if (tv_out) *tv_out = tv;
+  return FOT_OK;
+}
+
+// the marginal violation sum |Gamma 1 - a| of the context's iterate (f, psi) at eps_last: the
+// measurement of fot_solve_tol (synchronising)
+static fot_status source_violation(fot_ctx* c, double* tv) {
+  half_step(c, c->psi, c->la, c->eps_last, c->tmp2, c->tmp);
+  double* out = c->red + 4 * c->red_blocks;
+  source_stats(c, c->f, c->tmp, c->eps_last, out);
+  double h[3];
+  FOT_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  fot_status s = read_latched(c);
+  if (s != FOT_OK) return s;
+  *tv = h[0];
+  return isfinite(h[0]) ? FOT_OK : FOT_ENONFINITE;
+}
+
+fot_status fot_select_eps(fot_ctx* c, const float* g, const float* G, double dx, const double* cand,
+                          int n_cand, int eps_units, int probe_iters, int check_every,
+                          double min_decrease, int use_cfot, int* index_out, double* tv_out) {
+  if (!c || bad_ptr(g) || bad_ptr(G) || !cand || n_cand < 1 || !index_out) return FOT_EINVAL;
+  if (check_every < 1 || probe_iters <= check_every || !(min_decrease >= 0.0) || !(min_decrease < 1.0))
+    return FOT_EINVAL;
+  if (eps_units != FOT_EPS_PX2 && eps_units != FOT_EPS_PAPER) return FOT_EINVAL;
+  if (!isfinite(dx)) return FOT_EINVAL;
+  for (int i = 0; i < n_cand; ++i)
+    if (!(cand[i] > 0.0) || !isfinite(cand[i])) return FOT_EINVAL;
+  if (use_cfot && !cfot_supported(c->rows, c->cols)) return FOT_EUNSUPPORTED;
+  *index_out = -1;
+  std::vector<int> order((size_t)n_cand);
+  for (int i = 0; i < n_cand; ++i) order[(size_t)i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return cand[x] < cand[y]; });
+  for (int i : order) {
+    const double e = cand[i];
+    // the first check_every iterations, then the rest of the probe from the same start
+    double tv1 = INFINITY, tv2 = INFINITY;
+    fot_status s = use_cfot ? fot_cfot_solve(c, g, G, dx, &e, 1, eps_units, check_every)
+                            : fot_solve(c, g, G, dx, &e, 1, eps_units, check_every);
+    if (s == FOT_OK) s = source_violation(c, &tv1);
+    if (s == FOT_OK)
+      s = use_cfot ? fot_cfot_solve(c, g, G, dx, &e, 1, eps_units, probe_iters)
+                   : fot_resume(c, &e, 1, eps_units, probe_iters - check_every);
+    if (s == FOT_OK) s = source_violation(c, &tv2);
+    if (s == FOT_ENONFINITE) continue;               // unstable at this eps: try the next larger
+    if (s != FOT_OK) return s;
+    if (tv2 <= (1.0 - min_decrease) * tv1) {
+      *index_out = i;
+      if (tv_out) *tv_out = tv2;
+      return FOT_OK;
+    }
+  }
   return FOT_OK;
 }
 

@@ -59,6 +59,7 @@ struct BandTable {
   float* slots;
   int slot_chunks;
   int spin_limit;
+  int tc_single;                         // tensor pass: single BF16 operands (one MMA per term)
   BandArgs p[MAXP];
 };
 static_assert(sizeof(BandTable<kMaxBatch>) <= 32764, "kernel parameter limit");

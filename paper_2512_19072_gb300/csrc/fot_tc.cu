@@ -234,23 +234,22 @@ __device__ __forceinline__ void store_split8(const float* v, unsigned char* hi_p
   *reinterpret_cast<uint4*>(lo_p) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
 }
 
+// the hi part only (single BF16 operands)
+__device__ __forceinline__ void store_hi8(const float* v, unsigned char* hi_p) {
+  uint32_t hw[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    hw[i] = *reinterpret_cast<const uint32_t*>(&h2);
+  }
+  *reinterpret_cast<uint4*>(hi_p) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+}
+
 // tensor-memory load / store of N consecutive 32-bit columns of this warp's 32 lanes
 template <int N> __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v);
 template <> __device__ __forceinline__ void tmem_ld<4>(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr));
-}
-template <> __device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr));
-}
-template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
 }
 // Wait for this thread's tensor-memory loads and pin their destination registers: the
 // registers pass through the wait as read-write operands, so no use of them can be scheduled
@@ -258,15 +257,6 @@ template <> __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, uint32_t
 template <int N> __device__ __forceinline__ void reg_pin(uint32_t* v);
 template <> __device__ __forceinline__ void reg_pin<4>(uint32_t* v) {
   asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]) :: "memory");
-}
-template <> __device__ __forceinline__ void reg_pin<8>(uint32_t* v) {
-  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]) :: "memory");
-}
-template <> __device__ __forceinline__ void reg_pin<16>(uint32_t* v) {
-  asm volatile(""
-               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
-                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
-               :: "memory");
 }
 template <int N> __device__ __forceinline__ void tmem_wait_ld(uint32_t* a) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -282,18 +272,6 @@ template <int N> __device__ __forceinline__ void tmem_st(uint32_t taddr, const u
 template <> __device__ __forceinline__ void tmem_st<4>(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
                :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
-}
-template <> __device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const uint32_t* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-               :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
-}
-template <> __device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-      :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-         "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
 }
 
 // the CTA holding stage x of the pass when S stages are shared out over C CTAs (CTA k takes
@@ -362,6 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int C = (int)gridDim.x, cta = (int)blockIdx.x;
   const int spin = tab.spin_limit;
+  const bool single = tab.tc_single != 0;               // one BF16 MMA per term (FOT_BF16)
   volatile int* abort_flag = &s_abort;
   int* err0 = tab.p[0].err;
 
@@ -609,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue (one lane)
     if (lane == 0) {
-      const uint32_t idesc1 = instr_desc(kTM, 2 * TN), idesc2 = instr_desc(kTM, TN);
+      const uint32_t idesc1 = instr_desc(kTM, single ? TN : 2 * TN), idesc2 = instr_desc(kTM, TN);
       int oi = 0, ai = 0;
       bool ok = true;
       for (int i = 0; i < np && ok; ++i) {
@@ -635,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
               const uint64_t dAl = smem_desc(sAlo + ks * 256, 128, kGroupBytes);
               const uint64_t dB = smem_desc(sB + ks * 256, 128, kGroupBytes);
               mma_bf16(dcol, dAh, dB, idesc1, (ch > s0 || ks > 0) ? 1u : 0u);   // hi x [B_hi | B_lo]
-              mma_bf16(dcol, dAl, dB, idesc2, 1u);                               // lo x B_hi
+              if (!single) mma_bf16(dcol, dAl, dB, idesc2, 1u);                  // lo x B_hi
             }
             mma_commit(smem_u32(&opempty[so]));
             issued_mma = 1;
@@ -696,7 +675,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
               v[j] = (m0 + j < len) ? ex2(fmaf(xs[j], sc, K)) : 0.f;   // x = -inf -> 0
             }
           }
-          store_split8(v, stp + aoff + g * 128, stp + kABytes + aoff + g * 128);
+          if (single)
+            store_hi8(v, stp + aoff + g * 128);
+          else
+            store_split8(v, stp + aoff + g * 128, stp + kABytes + aoff + g * 128);
         }
         // one proxy fence orders this thread's generic accesses of the stage against the async
         // proxy: its A stores before the MMA reads them, and its reads of the x slot (and of
@@ -819,11 +801,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_pass_kernel(const __grid_const
         for (int c0 = hcol; c0 < hcol + HN; c0 += CH) {
           uint32_t d1[CH], d2[CH];
           tmem_ld<CH>(tacc + (uint32_t)c0, d1);
-          tmem_ld<CH>(tacc + (uint32_t)(TN + c0), d2);
+          if (!single) tmem_ld<CH>(tacc + (uint32_t)(TN + c0), d2);
           tmem_wait_ld<CH>(d1, d2);
           float cv[CH];
 #pragma unroll
-          for (int u = 0; u < CH; ++u) cv[u] = __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
+          for (int u = 0; u < CH; ++u) cv[u] = single ? __uint_as_float(d1[u]) : __uint_as_float(d1[u]) + __uint_as_float(d2[u]);
           if (p.split) {
 #pragma unroll
             for (int u = 0; u < CH; u += 4)
@@ -1242,6 +1224,7 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx) {
       tt->slots = ts->slots;
       tt->slot_chunks = ts->slot_chunks;
       tt->spin_limit = ts->spin;
+      tt->tc_single = tctx[0]->precision == FOT_BF16 ? 1 : 0;
       const int grid = std::max(1, std::min(sms, tt->ctas));
       ktimer_begin(s, kKTensor);
       if (tw == 64)

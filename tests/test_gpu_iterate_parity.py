@@ -26,6 +26,11 @@ pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore:invalid value 
 # split-BF16 products (hi*hi + hi*lo + lo*hi) miss < 2^-16 relative per term: each of the two
 # passes of a half-step adds < 2^-16 / ln 2 to a log2 output, i.e. |df| <= 2^-15 eps
 MIXED_HALF_STEP = 2.0 ** -15
+# single BF16 operands (FOT_BF16): each operand rounded to 8 significant bits (relative error
+# <= 2^-8), a product within 2^-7 + 2^-16 relative, so each window sum within delta = 2^-7
+# (1 + 2^-9) relative; each of the two passes of a half-step moves S by at most delta (natural
+# log units): |df| <= 2 delta eps = 2^-6 (1 + 2^-9) eps
+BF16_HALF_STEP = 2.0 ** -6 * (1 + 2.0 ** -9)
 
 
 def _sampled_lse(pot, eps, samples):
@@ -51,11 +56,15 @@ def _solve(B, n, prec):
     return w, g, G, ctx
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+def _prec(B, name):
+    return {"fp32": B.FOT_FP32, "mixed": B.FOT_MIXED, "bf16": B.FOT_BF16}[name]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed", "bf16"])
 @pytest.mark.parametrize("n", [1024, 2048])
 def test_iterate_half_steps_sampled(fot_lib, n, prec):
     B = fot_lib
-    w, g, G, ctx = _solve(B, n, B.FOT_FP32 if prec == "fp32" else B.FOT_MIXED)
+    w, g, G, ctx = _solve(B, n, _prec(B, prec))
     eps = float(w.eps[-1])
     f_it, psi_it = (to_np(t) for t in B.fot_potentials(ctx))
     # one more u-half from the iterate's psi, and one more v-half from its f
@@ -76,7 +85,7 @@ def test_iterate_half_steps_sampled(fot_lib, n, prec):
                 assert abs(lse_gpu[j, k] - S) <= POT_RTOL * lse_scale, ((j, k), lse_gpu[j, k], S)
                 tol = POT_RTOL * out_scale
             else:
-                tol = POT_RTOL * out_scale + MIXED_HALF_STEP * eps
+                tol = POT_RTOL * out_scale + (MIXED_HALF_STEP if prec == "mixed" else BF16_HALF_STEP) * eps
             if np.isfinite(o_ref):
                 assert abs(out_gpu[j, k] - o_ref) <= tol, ((j, k), out_gpu[j, k], o_ref, tol)
             else:
@@ -91,7 +100,7 @@ def test_full_size_phase_from_gpu_potentials(fot_lib, prec):
     is taken)."""
     B = fot_lib
     n = 1024
-    w, g, G, ctx = _solve(B, n, B.FOT_FP32 if prec == "fp32" else B.FOT_MIXED)
+    w, g, G, ctx = _solve(B, n, _prec(B, prec))
     eps = float(w.eps[-1])
     dx = 1.0 / math.sqrt(n)
     f_gpu, psi_gpu = (to_np(t) for t in B.fot_potentials(ctx))
@@ -109,17 +118,25 @@ def test_full_size_phase_from_gpu_potentials(fot_lib, prec):
     assert (err <= bound).all(), (err.max(), bound[err > bound].min())
 
 
-def test_mixed_solve_256_matches_oracle(fot_lib):
-    """Config 3 at 256^2, 200 iterations, mixed form, against the oracle's FP64 iterate.
-
-    Each update is 1-Lipschitz in the sup norm (a log-sum-exp of its input plus a constant), so
-    the split-BF16 error of each half-step (<= 2^-15 eps) adds at most linearly over the 2T
-    half-steps; the FP32 rounding adds as in the FP32 solve (solve_rtol)."""
-    B = fot_lib
+@pytest.fixture(scope="module")
+def c3_256_ref():
     w = inputs.config3(256)
     g, G = f32(w.g), f32(w.G)
-    r = fot.fot_iterate(g, G, w.eps, w.iters)
-    ctx = B.fot_create(256, 256, B.FOT_MIXED)
+    return w, g, G, fot.fot_iterate(g, G, w.eps, w.iters)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16"])
+def test_tensor_solve_256_matches_oracle(fot_lib, c3_256_ref, prec):
+    """Config 3 at 256^2, 200 iterations, tensor-core forms, against the oracle's FP64 iterate.
+
+    Each update is 1-Lipschitz in the sup norm (a log-sum-exp of its input plus a constant), so
+    the operand rounding error of each half-step (2^-15 eps for split BF16, 2^-7 eps for single
+    BF16) adds at most linearly over the 2T half-steps; the FP32 rounding adds as in the FP32
+    solve (solve_rtol)."""
+    B = fot_lib
+    w, g, G, r = c3_256_ref
+    step = MIXED_HALF_STEP if prec == "mixed" else BF16_HALF_STEP
+    ctx = B.fot_create(256, 256, _prec(B, prec))
     B.fot_solve(ctx, to_dev(g), to_dev(G), w.eps, w.iters)
     f, psi = (to_np(t) for t in B.fot_potentials(ctx))
     _, tensor_terms = B.fot_work_count(ctx, tensor=True)
@@ -128,10 +145,10 @@ def test_mixed_solve_256_matches_oracle(fot_lib):
         fin = np.isfinite(ref)
         assert np.array_equal(np.isneginf(gpu), np.isneginf(ref)), what
         scale = np.abs(ref[fin]).max()
-        tol = 2 * w.iters * MIXED_HALF_STEP * float(np.max(w.eps)) + solve_rtol(w.iters) * scale
+        tol = 2 * w.iters * step * float(np.max(w.eps)) + solve_rtol(w.iters) * scale
         err = np.abs(gpu[fin] - ref[fin]).max()
         assert err <= tol, (what, err, tol)
     l1, _ = B.fot_marginal_error(ctx)
     l1_ref = fot.marginal_l1(r["f"], r["psi"], r["a"], r["b"], r["eps_last"])
-    assert abs(l1 - l1_ref) <= 1e-3 + 1e-2 * l1_ref
+    assert abs(l1 - l1_ref) <= (1e-3 if prec == "mixed" else 2e-2) + 1e-2 * l1_ref
     ctx.close()
