@@ -233,7 +233,12 @@ N_SM = 152
 # capture of the current build on the benchmark workload (the capture and its command are in the
 # named profiles/ summary).  Keyed by (kernel, n, precision); a kernel that changes since its
 # capture must lose its entry (the bench line then reports traffic null).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("tc_pass_kernel", 1024, "mixed"): {
+        "bytes": (4.548096e6 + 0.0 + 8.751104e6 + 5.376e3) / 2,
+        "source": "ncu --set full, one row-pass and one column-pass launch (mean), "
+                  "profiles/tc_pass_kernel_c3_1024_mixed.md"},
+}
 
 
 def _roofline(n, a, ktimes, work, loop_ms):
