@@ -80,7 +80,8 @@ constexpr int kGroupBytes = (kKC / 8) * 128;   // 512 B between 8-row core-matri
 constexpr float kTiltMaxTC = 48.f;
 constexpr int kMaxPieces = 128;          // units one CTA's share may touch
 constexpr int kChunk = 4;                // stages per accumulation chunk
-constexpr int kMaxDecl = 128;            // CUDA-core items (16 rows x 16 outputs) per CTA
+constexpr int kMaxDecl = 1024;           // CUDA-core items (16 rows x 16 outputs) per CTA: every
+                                         // unit of the largest table declined, dealt over 152 CTAs
 constexpr int kUnitsPerThread = 8;       // units each thread holds during the set-up scan
 constexpr int kSpinDefault = 1 << 20;    // bounded mbarrier polls
 constexpr int kRouteKC = 64;             // window rounding of the host's tile-width estimate
@@ -100,7 +101,7 @@ template <int TN> struct TcShape {
   static constexpr int kEpiSlot = kAlphaBytes + kLmBytes;
   static constexpr int kOpOff = kEpiOff + kEpiBufs * kEpiSlot;
   static constexpr int kSmemBytes = kOpOff + kOpStages * kOpBytes + 1024;
-  static_assert(kSmemBytes <= 227 * 1024 - 8 * 1024, "shared memory per CTA (dynamic + static)");
+  static_assert(kSmemBytes <= 227 * 1024 - 12 * 1024, "shared memory per CTA (dynamic + static)");
   // 2 accumulators of 2TN columns, then the TN-column running sum of a unit's chunks
   static constexpr uint32_t kTmemCols = 5 * TN <= 32 ? 32 : 5 * TN <= 64 ? 64 : 5 * TN <= 128 ? 128 : 5 * TN <= 256 ? 256 : 512;
 };
@@ -1201,7 +1202,9 @@ int tc_pass(cudaStream_t s, BandTable<MAXP>& t, int tw, fot_ctx* const* ctx) {
     const int sms = ts->sms;
     int smax_all = 1;
     for (int q = 0; q < tt->n; ++q) smax_all = std::max(smax_all, tt->p[q].s_max);
+    const long long items_max = (long long)tt->ctas * (kTM / (2 * kBR)) * (tw / kBT);
     if (tt->ctas > kThreads * kUnitsPerThread || tt->ctas > (kMaxPieces / 2) * sms ||
+        items_max > (long long)kMaxDecl * std::min(sms, tt->ctas) ||
         (uint64_t)tt->ctas * (uint64_t)smax_all * (uint64_t)sms >= (1ull << 32)) {
       // more units than the kernel's set-up holds (or stage positions beyond its 32-bit
       // partition arithmetic): the CUDA-core sums for all of them
