@@ -143,6 +143,27 @@ fot_status fot_select_eps(fot_ctx* ctx, const float* g, const float* G, double d
                           int n_cand, int eps_units, int probe_iters, int check_every,
                           double min_decrease, int use_cfot, int* index_out, double* tv_out);
 
+/* Algorithm 1 between an input grid and an output grid of different sizes (Sec. 2: square,
+ * equal arrays are not essential).  Both planes have unit pixel spacing and are centre-aligned,
+ * x_j = j - (rows_in - 1)/2 and X_L = L - (rows_out - 1)/2 (columns likewise), so the cost
+ * C_jkLM = ((x_j - X_L)^2 + (y_k - Y_M)^2)/2 still separates and each Lambda factor of Eqs. 7-8
+ * is a rectangular rows_in x rows_out (cols_in x cols_out) matrix:
+ *     f   = eps (log a - log(Lambda_r V Lambda_c^T))    on the input grid,
+ *     psi = eps (log b - log(Lambda_r^T u Lambda_c))    on the output grid,
+ * a = g^2/sum g^2, b = G^2/sum G^2, start V = 1/(rows_out cols_out).  Every axis pass is dense
+ * and exact in FP32 (each output's own maximum, then the sum), as FOT_FP32_DENSE.
+ *   g: rows_in x cols_in and G: rows_out x cols_out amplitudes, row-major FP32 device memory;
+ *   eps in px^2 (n_eps == 1, or n_eps == iters for one value per iteration); f_out
+ *   (rows_in x cols_in) and psi_out (rows_out x cols_out): device buffers of the caller that
+ *   receive the potentials (px^2, -inf at zero mass); cuda_stream: the stream (NULL: default).
+ * The call allocates and frees its temporaries (3 images and a few words) and synchronises the
+ * stream before returning.  Errors: FOT_EINVAL (a null pointer, a size < 1 or > 3072,
+ * iters < 1, n_eps other than 1 or iters, eps not finite and > 0), FOT_EMASS (g or G without
+ * mass), FOT_ENOMEM, FOT_ENONFINITE (a non-finite potential), FOT_ECUDA. */
+fot_status fot_solve_rect(const float* g, int rows_in, int cols_in, const float* G, int rows_out,
+                          int cols_out, const double* eps, int n_eps, int iters, float* f_out,
+                          float* psi_out, void* cuda_stream);
+
 /* cFOT (Sec. 3.1): the same problem, start and eps rules as fot_solve, but the iterations run
  * Algorithm 1 in the exponential domain with every Lambda product replaced by a linear
  * convolution with lambda_j = exp(-j^2 / (2 eps)), j = -(n-1) .. n-1, along the columns and

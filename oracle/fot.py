@@ -21,7 +21,8 @@ Units and notation (pixel units throughout):
     normalised to equal, unit mass).
 
 Parity status: every function below is pinned by a -m "not gpu" test
-(tests/test_oracle_pins.py); none is "parity unpinned".
+(tests/test_oracle_pins.py); none is "parity unpinned".  The unequal-grid form is in
+oracle/rect.py (pins in tests/test_oracle_rect.py).
 """
 from __future__ import annotations
 

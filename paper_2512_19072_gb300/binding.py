@@ -46,6 +46,7 @@ _SIGS = {
     "fot_cfot_solve": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I]),
     "fot_solve_tol": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
     "fot_select_eps": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
+    "fot_solve_rect": (_I, [_P, _I, _I, _P, _I, _I, _DP, _I, _I, _P, _P, _P]),
     "fot_sync": (_I, [_P]),
     "fot_potentials": (_I, [_P, _P, _P]),
     "fot_set_potentials": (_I, [_P, _P, _P]),
@@ -188,6 +189,20 @@ def fot_select_eps(ctx, g, G, candidates, probe_iters, check_every, min_decrease
                                int(probe_iters), int(check_every), float(min_decrease), int(bool(use_cfot)),
                                ctypes.byref(idx), ctypes.byref(tv)), "fot_select_eps")
     return idx.value, tv.value
+
+
+def fot_solve_rect(g, G, eps, iters=None):
+    """Algorithm 1 between the grid of g (input) and the grid of G (output), both float32 CUDA
+    tensors; returns (f on the input grid, psi on the output grid)."""
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    f = torch.empty_like(g)
+    psi = torch.empty_like(G)
+    (ri, ci), (ro, co) = g.shape, G.shape
+    _check(_lib.fot_solve_rect(_ptr(g), ri, ci, _ptr(G), ro, co, ep, ne, int(iters), _ptr(f), _ptr(psi),
+                               _stream()), "fot_solve_rect")
+    return f, psi
 
 
 def fot_resume(ctx, eps, iters=None, eps_units=FOT_EPS_PX2):
