@@ -46,7 +46,14 @@
 // (and kap^2 c <= 32).  The largest term of every output then has A >= 2^-96 (alpha is at most
 // the largest term at kc), and the A values that flush below 2^-126 add less than W 2^-30
 // relative.  Other units (and units whose rows carry no mass) are summed on the CUDA cores by
-// the producer warps after the tensor work (the banded pass's window sums, 16 rows per warp).
+// the producer warps after the tensor work, as 16-row x 16-output items dealt round-robin over
+// all CTAs: each item takes its rows' exact maxima at its own centre, then the banded pass's
+// tilted FP32 GEMM (or exact window sums where the item's own tilt bound fails too).
+//
+// Shared-memory hand-offs between the generic proxy (thread loads and stores) and the async
+// proxy (TMA writes, MMA reads) are ordered by fence.proxy.async.shared::cta on the thread
+// side, in both directions: after a thread's A stores (before the MMA reads them) and after its
+// reads of an x tile or an epilogue slot (before the next tensor copy overwrites it).
 #include "fot_band_item.cuh"
 
 #include <cuda.h>
@@ -195,7 +202,7 @@ __device__ __forceinline__ void mbar_drain(uint32_t mbar, uint32_t parity) {
     if (mbar_try(mbar, parity)) return;
 }
 
-// AND of pred over the 128 epilogue threads (named barrier 2): a decision they all take alike
+// AND of pred over the kEpi epilogue threads (named barrier 2): a decision they all take alike
 __device__ __forceinline__ bool epi_all(bool pred) {
   uint32_t r;
   asm volatile(
