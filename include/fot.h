@@ -164,6 +164,13 @@ fot_status fot_solve_rect(const float* g, int rows_in, int cols_in, const float*
                           int cols_out, const double* eps, int n_eps, int iters, float* f_out,
                           float* psi_out, void* cuda_stream);
 
+/* The same solve in FP64 throughout (a GPU reference form, for equal or unequal grids; FP64
+ * inputs and outputs, sizes up to 1536 per axis, the arithmetic of the CUDA math library's
+ * exp2 / log2 in double precision).  Arguments, ownership and errors as fot_solve_rect. */
+fot_status fot_solve_rect_fp64(const double* g, int rows_in, int cols_in, const double* G, int rows_out,
+                               int cols_out, const double* eps, int n_eps, int iters, double* f_out,
+                               double* psi_out, void* cuda_stream);
+
 /* cFOT (Sec. 3.1): the same problem, start and eps rules as fot_solve, but the iterations run
  * Algorithm 1 in the exponential domain with every Lambda product replaced by a linear
  * convolution with lambda_j = exp(-j^2 / (2 eps)), j = -(n-1) .. n-1, along the columns and

@@ -47,6 +47,7 @@ _SIGS = {
     "fot_solve_tol": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
     "fot_select_eps": (_I, [_P, _P, _P, _D, _DP, _I, _I, _I, _I, _D, _I, ctypes.POINTER(_I), _DP]),
     "fot_solve_rect": (_I, [_P, _I, _I, _P, _I, _I, _DP, _I, _I, _P, _P, _P]),
+    "fot_solve_rect_fp64": (_I, [_P, _I, _I, _P, _I, _I, _DP, _I, _I, _P, _P, _P]),
     "fot_sync": (_I, [_P]),
     "fot_potentials": (_I, [_P, _P, _P]),
     "fot_set_potentials": (_I, [_P, _P, _P]),
@@ -202,6 +203,25 @@ def fot_solve_rect(g, G, eps, iters=None):
     (ri, ci), (ro, co) = g.shape, G.shape
     _check(_lib.fot_solve_rect(_ptr(g), ri, ci, _ptr(G), ro, co, ep, ne, int(iters), _ptr(f), _ptr(psi),
                                _stream()), "fot_solve_rect")
+    return f, psi
+
+
+def _ptr64(t):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fot_solve_rect_fp64(g, G, eps, iters=None):
+    """FP64 form of fot_solve_rect (float64 CUDA tensors in and out)."""
+    e, ep, ne = _eps_arr(eps)
+    if iters is None:
+        iters = ne
+    f = torch.empty_like(g)
+    psi = torch.empty_like(G)
+    (ri, ci), (ro, co) = g.shape, G.shape
+    _check(_lib.fot_solve_rect_fp64(_ptr64(g), ri, ci, _ptr64(G), ro, co, ep, ne, int(iters), _ptr64(f),
+                                    _ptr64(psi), _stream()), "fot_solve_rect_fp64")
     return f, psi
 
 

@@ -63,3 +63,20 @@ def test_rect_arguments(fot_lib):
         B.fot_solve_rect(g, to_dev(_amp(rng, (6, 6), "gauss")), [-1.0], 5)  # eps <= 0
     with pytest.raises(B.FotError):
         B.fot_solve_rect(g, to_dev(_amp(rng, (6, 6), "gauss")), [2.0, 3.0], 5)   # n_eps mismatch
+
+
+@pytest.mark.parametrize("shapes", [((40, 50), (56, 36)), ((64, 64), (64, 64))])
+def test_rect_fp64_reference_matches_oracle(fot_lib, shapes):
+    """The FP64 GPU reference form: the oracle's FP64 iterate to ~1e-12 (both compute the same
+    sums in double precision; only the order of additions and the library exp / log differ)."""
+    import torch
+    B = fot_lib
+    si, so = shapes
+    rng = np.random.default_rng(11)
+    g = _amp(rng, si, "gauss", 0.05)
+    G = _amp(rng, so, "disk", 0.05)
+    eps = [6.0]
+    f, psi = B.fot_solve_rect_fp64(torch.from_numpy(g).cuda(), torch.from_numpy(G).cuda(), eps, 50)
+    r = rect.fot_iterate_rect(g, G, eps, 50)
+    assert_pot_close(f.cpu().numpy(), r["f"], rtol=1e-11, what="f")
+    assert_pot_close(psi.cpu().numpy(), r["psi"], rtol=1e-11, what="psi")
