@@ -7,6 +7,8 @@ all device allocations); it keeps its intermediate in a static device array inst
 This file sorts last so that a run stopping at the first failure has run every other
 test first.
 """
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -69,12 +71,19 @@ def test_noalloc_allocates_nothing(fot_lib):
     S = torch.empty(shape, device="cuda")
     B.fot_u_update_noalloc(psi, la, eps, f_out=f, logsum_out=S)     # warm-up
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    alloc0 = torch.cuda.memory_allocated()
-    for _ in range(3):
-        B.fot_u_update_noalloc(psi, la, eps, f_out=f, logsum_out=S)
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert torch.cuda.memory_allocated() == alloc0
+    # tensors left by earlier tests must not be collected (freed) inside the measured window
+    gc.collect()
+    gc.disable()
+    try:
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(3):
+            B.fot_u_update_noalloc(psi, la, eps, f_out=f, logsum_out=S)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        alloc1 = torch.cuda.memory_allocated()
+    finally:
+        gc.enable()
+    assert alloc1 == alloc0
     assert free1 == free0, (free0, free1)
     assert torch.isfinite(f[torch.isfinite(la)]).all()
